@@ -1,0 +1,162 @@
+/*
+ * ssa.h -- C ABI of the GB300 fast Basic SSA library (libssa_gb300.so).
+ *
+ * Implements the hot path of "Computation- and Space-Efficient
+ * Implementation of SSA" (Korobeynikov): the trajectory-matrix products X v
+ * and X^T u by FFT against a cached spectrum of the series (section 4,
+ * Algorithms 2 and 3), the Golub-Kahan-Lanczos truncated SVD with full
+ * reorthogonalisation and thick restart that they drive (section 3,
+ * Algorithm 1), and grouped rank-1 Hankelization by FFT convolution
+ * (section 5, Algorithm 4; sections 2.3-2.4 for grouping and diagonal
+ * averaging).  The trajectory matrix is never formed.
+ *
+ * Conventions
+ *   - Series f[0..N-1] is the paper's f_1..f_N; window L with 1 < L < N,
+ *     K = N - L + 1; X is the L x K Hankel matrix X[i][j] = f[i+j].
+ *   - Matrices are column-major doubles; U is L x k, V is K x k.
+ *   - Singular values are returned in descending order.  Each pair
+ *     (u_i, v_i) is signed so that the entry of u_i with the largest
+ *     magnitude is positive (lowest index among equals).
+ *   - Every pointer argument may be host memory or device memory of the
+ *     current CUDA device; the library detects which.  Buffers are owned by
+ *     the caller; handles (plans, decompositions) are owned by the library
+ *     until destroyed.  Inputs are never modified.
+ *   - All GPU work is issued on opts->stream (NULL = the legacy default
+ *     stream).  A call returns after its results are complete, except that
+ *     ssa_matvec / ssa_hankelize with only device pointers return once the
+ *     work is enqueued on the stream.
+ *   - Calls return SSA_OK (0) or a positive error code; ssa_strerror()
+ *     names it and ssa_last_error() gives a detail message for the calling
+ *     thread.  Handles stay valid after an error.  Calls on one plan are not
+ *     thread-safe; use one plan per thread.
+ *
+ * Precision (see SSA_PREC_*): GB300's FP64 pipe runs at about 1/68 of the
+ * FP32 rate, so "F64" results are computed in double-float arithmetic
+ * (an unevaluated sum of two floats, ~48 significant bits) on the FP32
+ * pipes; inputs and outputs are IEEE doubles.
+ */
+#ifndef SSA_GB300_H
+#define SSA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SSA_OK 0
+#define SSA_EINVAL 1      /* invalid argument (sizes, k, groups, pointers) */
+#define SSA_ENOMEM 2      /* device allocation failed */
+#define SSA_ENOCONV 3     /* Lanczos did not converge within max_restarts; results and residuals are still returned */
+#define SSA_ETIMEOUT 4    /* a bounded device wait ran out (batched / serving front-ends) */
+#define SSA_ECUDA 5       /* CUDA runtime error */
+#define SSA_ENUMERIC 6    /* non-finite value met (input or overflow) */
+
+/* precision modes */
+#define SSA_PREC_F64 0    /* all steps in double-float (FP64-class accuracy) */
+#define SSA_PREC_F32C 1   /* FFT products in FP32 with the spectrum multiply compensated
+                             (spectrum kept in double-float); reorthogonalisation, the
+                             projected SVD and the convergence test stay double-float */
+
+typedef struct ssa_plan_s* ssa_plan_t;
+typedef struct ssa_decomp_s* ssa_decomp_t;
+
+typedef struct ssa_opts {
+  int precision;      /* SSA_PREC_F64 or SSA_PREC_F32C */
+  double tol;         /* convergence: every wanted Ritz residual <= tol * sigma_1 (0 = default for the precision) */
+  int max_restarts;   /* thick restarts before SSA_ENOCONV (default 200) */
+  int krylov_dim;     /* Krylov dimension d (0 = min(max(2k, k+32), min(L, K)); at most 510) */
+  int keep;           /* Ritz pairs kept per restart (0 = k + ceil((d-k)/2)) */
+  uint64_t seed;      /* splitmix64 seed of the starting vector p_0 and breakdown vectors */
+  void* stream;       /* cudaStream_t for all GPU work (NULL = default stream) */
+} ssa_opts_t;
+
+/* Fill *opts with defaults: SSA_PREC_F64, tol 0 (precision default), 200 restarts, seed 0, NULL stream. */
+void ssa_default_opts(ssa_opts_t* opts);
+
+/*
+ * Embedding step (section 2.1) without forming X: validate N > 2 and
+ * 1 < L < N, pick the FFT length M (the least power of two >= N; any M >= N
+ * is exact once M - N zeros separate the two blocks of c, Algorithm 2 step
+ * 1) and allocate the plan's device tables.  opts may be NULL (defaults).
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA.
+ */
+int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_plan_t* out);
+
+/* FFT geometry of a plan: *M (FFT length), *single_cta (1 when each transform runs in one CTA). */
+int ssa_plan_info(ssa_plan_t plan, int64_t* M, int* single_cta);
+
+/*
+ * Cache the spectrum c-hat = FFT_M(c) of the circulant column
+ * c = (f_{N-L+1}, ..., f_N, 0 x (M-N), f_1, ..., f_{N-L}) (Algorithm 2
+ * steps 1-2).  f: N doubles.  When L > K the plan works on X^T, the
+ * K-trajectory matrix of the same series, so c uses window min(L, K).
+ * Errors: SSA_EINVAL (null), SSA_ENUMERIC (non-finite f), SSA_ECUDA.
+ */
+int ssa_set_series(ssa_plan_t plan, const double* f);
+
+/* Copy the cached spectrum C-hat_0..C-hat_{M/2} (M/2 + 1 values) to re / im (natural order, unscaled). */
+int ssa_get_spectrum(ssa_plan_t plan, double* re, double* im);
+
+/*
+ * Trajectory-matrix products for nvec vectors (Algorithm 2 for transpose =
+ * 0: y_j = X x_j, x_j of length K, y_j of length L; Algorithm 3 for
+ * transpose = 1: y_j = X^T x_j, x_j of length L, y_j of length K).
+ * x and y hold the nvec vectors back to back.  Requires ssa_set_series.
+ * Errors: SSA_EINVAL, SSA_ECUDA.
+ */
+int ssa_matvec(ssa_plan_t plan, int transpose, const double* x, double* y, int nvec);
+
+/*
+ * Truncated SVD step (section 2.2 via section 3): the k leading singular
+ * triples of X by Golub-Kahan-Lanczos bidiagonalisation (Algorithm 1) with
+ * full reorthogonalisation (classical Gram-Schmidt applied twice, section
+ * 3.2.2) and thick restart (section 3.3), every product by Algorithms 2/3.
+ * f: N doubles, or NULL to reuse the series given to ssa_set_series.
+ * 1 <= k <= min(L, K).  On SSA_OK or SSA_ENOCONV *out holds a new
+ * decomposition (free it with ssa_decomp_destroy).
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ENOCONV, SSA_ENUMERIC, SSA_ECUDA.
+ */
+int ssa_decompose(ssa_plan_t plan, const double* f, int k, ssa_decomp_t* out);
+
+/* Decomposition facts: k, converged flag, thick restarts, X / X^T products applied, Krylov dimension d. */
+int ssa_decomp_info(ssa_decomp_t d, int* k, int* converged, int* restarts, int64_t* matvecs, int* krylov_dim);
+
+/*
+ * Copy results out: sigma (k), U (L x k), V (K x k), resid (k; the
+ * residual estimates |alpha_{c+1}| |P[r, i]| from relation (2)).  Any
+ * output pointer may be NULL to skip it.
+ */
+int ssa_decomp_get(ssa_decomp_t d, double* sigma, double* U, double* V, double* resid);
+
+/*
+ * Grouping and diagonal averaging (sections 2.3-2.4) of a decomposition:
+ * for group g the series of length N obtained by Hankelizing
+ * sum_{i in I_g} sigma_i u_i v_i^T, computed as Algorithm 4 (FFT
+ * convolution of u_i and v_i divided by the antidiagonal counts) summed in
+ * the frequency domain.  Groups are CSR: members of group g are
+ * grp_idx[grp_off[g] .. grp_off[g+1]-1], indices in [0, k), disjoint.
+ * out: m x N (group g at out + g*N).
+ * Errors: SSA_EINVAL (bad or overlapping groups), SSA_ECUDA.
+ */
+int ssa_reconstruct(ssa_decomp_t d, const int32_t* grp_off, const int32_t* grp_idx, int m, double* out);
+
+/*
+ * Algorithm 4 on caller-supplied triples: for each group the diagonal
+ * average of sum_i sigma_i u_i v_i^T.  sigma (r), U (L x r, leading
+ * dimension ldu >= L), V (K x r, ldv >= K); groups as in ssa_reconstruct
+ * with indices in [0, r).  out: m x N.
+ */
+int ssa_hankelize(ssa_plan_t plan, const double* sigma, const double* U, int64_t ldu, const double* V, int64_t ldv,
+                  int r, const int32_t* grp_off, const int32_t* grp_idx, int m, double* out);
+
+void ssa_plan_destroy(ssa_plan_t plan);
+void ssa_decomp_destroy(ssa_decomp_t d);
+const char* ssa_strerror(int code);
+const char* ssa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSA_GB300_H */

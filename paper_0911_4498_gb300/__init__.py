@@ -1,0 +1,13 @@
+"""GB300-native fast Basic SSA (arXiv:0911.4498): FFT-based trajectory-matrix
+products driving a thick-restart Golub-Kahan-Lanczos truncated SVD, and
+FFT-based grouped Hankelization, in hand-written CUDA for sm_103a.
+
+The compute lives in ``libssa_gb300.so`` (C ABI in ``include/ssa.h``);
+``paper_0911_4498_gb300._lib`` is its ctypes binding and
+``paper_0911_4498_gb300.build`` compiles it.  ``synth`` holds the seeded
+synthetic workloads.
+"""
+from ._lib import (SSA_ENOCONV, SSA_OK, SSA_PREC_F32C, SSA_PREC_F64, SSAError, groups_csr, lib, make_opts,  # noqa: F401
+                   ssa_decomp_destroy, ssa_decomp_get, ssa_decomp_info, ssa_decompose, ssa_default_opts,
+                   ssa_embed_plan, ssa_get_spectrum, ssa_hankelize, ssa_last_error, ssa_matvec, ssa_plan_destroy,
+                   ssa_plan_info, ssa_reconstruct, ssa_set_series, ssa_strerror)

@@ -1,0 +1,190 @@
+"""ctypes binding of libssa_gb300.so (include/ssa.h), argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Arrays may
+be numpy arrays (host memory) or torch CUDA tensors (device memory) of
+float64 (int32 for group arrays); the library detects which.  All compute
+happens in the CUDA library; if it is missing this module raises instead of
+falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libssa_gb300.so")
+
+SSA_OK, SSA_EINVAL, SSA_ENOMEM, SSA_ENOCONV, SSA_ETIMEOUT, SSA_ECUDA, SSA_ENUMERIC = range(7)
+SSA_PREC_F64, SSA_PREC_F32C = 0, 1
+
+
+class SsaOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
+                ("krylov_dim", ctypes.c_int), ("keep", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p)]
+
+
+class SSAError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_lib = None
+_VP, _I64, _I, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    "ssa_default_opts": (None, [ctypes.POINTER(SsaOpts)]),
+    "ssa_embed_plan": (_I, [_I64, _I64, ctypes.POINTER(SsaOpts), ctypes.POINTER(_VP)]),
+    "ssa_plan_info": (_I, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I)]),
+    "ssa_set_series": (_I, [_VP, _VP]),
+    "ssa_get_spectrum": (_I, [_VP, _VP, _VP]),
+    "ssa_matvec": (_I, [_VP, _I, _VP, _VP, _I]),
+    "ssa_decompose": (_I, [_VP, _VP, _I, ctypes.POINTER(_VP)]),
+    "ssa_decomp_info": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                             ctypes.POINTER(_I64), ctypes.POINTER(_I)]),
+    "ssa_decomp_get": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "ssa_reconstruct": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "ssa_hankelize": (_I, [_VP, _VP, _VP, _I64, _VP, _I64, _I, _VP, _VP, _I, _VP]),
+    "ssa_plan_destroy": (None, [_VP]),
+    "ssa_decomp_destroy": (None, [_VP]),
+    "ssa_strerror": (ctypes.c_char_p, [_I]),
+    "ssa_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_0911_4498_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int, allow=()):
+    if rc != SSA_OK and rc not in allow:
+        detail = lib().ssa_last_error().decode(errors="replace")
+        raise SSAError(rc, f"{lib().ssa_strerror(rc).decode()}: {detail}")
+    return rc
+
+
+def _ptr(x, dtype=np.float64):
+    """Raw pointer of a numpy array or torch tensor (contiguous, right dtype)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"need a C-contiguous {np.dtype(dtype)} array")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.int32
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"need a contiguous {want} tensor")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def ssa_default_opts() -> SsaOpts:
+    o = SsaOpts()
+    lib().ssa_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_opts(precision=SSA_PREC_F64, tol=0.0, max_restarts=200, krylov_dim=0, keep=0, seed=0, stream=None):
+    o = ssa_default_opts()
+    o.precision, o.tol, o.max_restarts = precision, tol, max_restarts
+    o.krylov_dim, o.keep, o.seed = krylov_dim, keep, seed
+    o.stream = stream
+    return o
+
+
+def ssa_embed_plan(N: int, L: int, opts: SsaOpts | None = None):
+    h = _VP()
+    _check(lib().ssa_embed_plan(N, L, ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
+    return h
+
+
+def ssa_plan_info(plan):
+    M, sc = _I64(), _I()
+    _check(lib().ssa_plan_info(plan, ctypes.byref(M), ctypes.byref(sc)))
+    return M.value, bool(sc.value)
+
+
+def ssa_set_series(plan, f):
+    _check(lib().ssa_set_series(plan, _ptr(f)))
+
+
+def ssa_get_spectrum(plan, re, im):
+    _check(lib().ssa_get_spectrum(plan, _ptr(re), _ptr(im)))
+
+
+def ssa_matvec(plan, transpose: int, x, y, nvec: int = 1):
+    _check(lib().ssa_matvec(plan, int(transpose), _ptr(x), _ptr(y), nvec))
+
+
+def ssa_decompose(plan, f, k: int):
+    """Returns (decomp handle, status); status is SSA_OK or SSA_ENOCONV."""
+    h = _VP()
+    rc = _check(lib().ssa_decompose(plan, _ptr(f), k, ctypes.byref(h)), allow=(SSA_ENOCONV,))
+    return h, rc
+
+
+def ssa_decomp_info(d):
+    k, conv, rs, kd = _I(), _I(), _I(), _I()
+    mv = _I64()
+    _check(lib().ssa_decomp_info(d, ctypes.byref(k), ctypes.byref(conv), ctypes.byref(rs), ctypes.byref(mv),
+                                 ctypes.byref(kd)))
+    return {"k": k.value, "converged": bool(conv.value), "restarts": rs.value, "matvecs": mv.value,
+            "krylov_dim": kd.value}
+
+
+def ssa_decomp_get(d, sigma=None, U=None, V=None, resid=None):
+    _check(lib().ssa_decomp_get(d, _ptr(sigma), _ptr(U), _ptr(V), _ptr(resid)))
+
+
+def ssa_reconstruct(d, grp_off, grp_idx, m: int, out):
+    _check(lib().ssa_reconstruct(d, _ptr(grp_off, np.int32), _ptr(grp_idx, np.int32), m, _ptr(out)))
+
+
+def ssa_hankelize(plan, sigma, U, ldu: int, V, ldv: int, r: int, grp_off, grp_idx, m: int, out):
+    _check(lib().ssa_hankelize(plan, _ptr(sigma), _ptr(U), ldu, _ptr(V), ldv, r, _ptr(grp_off, np.int32),
+                               _ptr(grp_idx, np.int32), m, _ptr(out)))
+
+
+def ssa_plan_destroy(plan):
+    lib().ssa_plan_destroy(plan)
+
+
+def ssa_decomp_destroy(d):
+    lib().ssa_decomp_destroy(d)
+
+
+def ssa_strerror(code: int) -> str:
+    return lib().ssa_strerror(code).decode()
+
+
+def ssa_last_error() -> str:
+    return lib().ssa_last_error().decode()
+
+
+def groups_csr(groups):
+    """CSR arrays (int32 offsets, int32 indices) for a list of index lists."""
+    off = np.zeros(len(groups) + 1, dtype=np.int32)
+    idx = []
+    for g, members in enumerate(groups):
+        idx.extend(int(i) for i in members)
+        off[g + 1] = len(idx)
+    return off, np.array(idx if idx else [0], dtype=np.int32)

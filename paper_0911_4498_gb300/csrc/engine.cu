@@ -1,0 +1,788 @@
+// Host engine and C ABI (include/ssa.h): plans, the spectrum of the series,
+// batched trajectory-matrix products, the thick-restart Golub-Kahan-Lanczos
+// driver (section 3) and grouped Hankelization (section 5).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "ssa.h"
+#include "lanczos.h"
+#include "spectral.h"
+
+using namespace ssa;
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512];
+static void set_err(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+#define CK(x)                                                                   \
+  do {                                                                          \
+    cudaError_t e_ = (x);                                                       \
+    if (e_ != cudaSuccess) {                                                    \
+      set_err("%s failed: %s (%s:%d)", #x, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA;         \
+    }                                                                           \
+  } while (0)
+#define CHECK_LAUNCH() CK(cudaGetLastError())
+#define REQ(cond, ...)           \
+  do {                           \
+    if (!(cond)) {               \
+      set_err(__VA_ARGS__);      \
+      return SSA_EINVAL;         \
+    }                            \
+  } while (0)
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller buffer: host buffers are staged through a
+// stream-ordered allocation (returned to the pool on release).
+template <class T>
+struct Staged {
+  T* dev = nullptr;
+  T* owned = nullptr;
+  const T* host_src = nullptr;
+  T* host_dst = nullptr;
+  size_t count = 0;
+  cudaStream_t s = nullptr;
+  int in(const T* p, size_t n, cudaStream_t st) {
+    s = st;
+    count = n;
+    if (is_device_ptr(p)) {
+      dev = const_cast<T*>(p);
+      return SSA_OK;
+    }
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&owned), n * sizeof(T) + 16, st));
+    CK(cudaMemcpyAsync(owned, p, n * sizeof(T), cudaMemcpyHostToDevice, st));
+    dev = owned;
+    return SSA_OK;
+  }
+  int out(T* p, size_t n, cudaStream_t st) {
+    s = st;
+    count = n;
+    if (is_device_ptr(p)) {
+      dev = p;
+      return SSA_OK;
+    }
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&owned), n * sizeof(T) + 16, st));
+    dev = owned;
+    host_dst = p;
+    return SSA_OK;
+  }
+  int finish() {
+    if (host_dst) CK(cudaMemcpyAsync(host_dst, dev, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    return SSA_OK;
+  }
+  bool needs_sync() const { return host_dst != nullptr; }
+  ~Staged() {
+    if (owned) cudaFreeAsync(owned, s);
+  }
+};
+
+// ------------------------------------------------------------------ tables
+// (cos, sin) of 2 pi m / P, reduced to the first octant so the double
+// cos/sin are evaluated on |theta| <= pi/4.
+static void cis_turn(int64_t m, int64_t P, double& c, double& s) {
+  m %= P;
+  if (m < 0) m += P;
+  if (P % 8 != 0) {
+    const double th = 2.0 * M_PI * (double)m / (double)P;
+    c = std::cos(th);
+    s = std::sin(th);
+    if (P == 1 || m == 0) { c = 1; s = 0; }
+    if (P == 2 && m == 1) { c = -1; s = 0; }
+    if (P == 4) {
+      const double cc[4] = {1, 0, -1, 0}, ss[4] = {0, 1, 0, -1};
+      c = cc[m];
+      s = ss[m];
+    }
+    return;
+  }
+  const int64_t q = P / 4;
+  const int quad = (int)(m / q);
+  int64_t rr = m - quad * q;  // angle within the quadrant, [0, P/4)
+  double c0, s0;
+  if (2 * rr <= q) {
+    const double th = 2.0 * M_PI * (double)rr / (double)P;
+    c0 = std::cos(th);
+    s0 = std::sin(th);
+  } else {
+    const double th = 2.0 * M_PI * (double)(q - rr) / (double)P;
+    c0 = std::sin(th);
+    s0 = std::cos(th);
+  }
+  switch (quad) {
+    case 0: c = c0; s = s0; break;
+    case 1: c = -s0; s = c0; break;
+    case 2: c = -c0; s = -s0; break;
+    default: c = s0; s = -c0; break;
+  }
+}
+
+static cplx<df64> tw_entry(int64_t m, int64_t P) {
+  double c, s;
+  cis_turn(m, P, c, s);
+  cplx<df64> z;
+  z.re = df_from_double(c);
+  z.im = df_from_double(-s);  // W_P^m = exp(-2 pi i m / P)
+  return z;
+}
+
+static int ilog2(int64_t x) {
+  int r = 0;
+  while (((int64_t)1 << r) < x) ++r;
+  return r;
+}
+
+// ------------------------------------------------------------------ handles
+struct Workspace {
+  int dcap = 0;
+  int64_t ldu = 0, ldv = 0;
+  df64* Ub[2] = {nullptr, nullptr};
+  df64* Vb[2] = {nullptr, nullptr};
+  df64* B = nullptr;
+  int ldb = 0;
+  df64* y = nullptr;
+  ReorthWork rw{};
+  SvdWork sw{};
+  df64* est = nullptr;
+  df64* dummy = nullptr;
+  int* flag = nullptr;
+  unsigned* status = nullptr;
+  int* sgn = nullptr;
+  std::map<int, int2*> sched;
+  void release() {
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(Ub[i]);
+      cudaFree(Vb[i]);
+      Ub[i] = Vb[i] = nullptr;
+    }
+    cudaFree(B);
+    cudaFree(y);
+    cudaFree(rw.part);
+    cudaFree(rw.h);
+    cudaFree(rw.nrm);
+    cudaFree(rw.counter);
+    cudaFree(sw.A);
+    cudaFree(sw.W);
+    cudaFree(sw.sigma);
+    cudaFree(sw.P);
+    cudaFree(sw.Q);
+    cudaFree(sw.resid);
+    cudaFree(sw.sigma_d);
+    cudaFree(sw.conv);
+    cudaFree(est);
+    cudaFree(dummy);
+    cudaFree(flag);
+    cudaFree(status);
+    cudaFree(sgn);
+    for (auto& kv : sched) cudaFree(kv.second);
+    sched.clear();
+    B = y = est = dummy = nullptr;
+    rw = ReorthWork{};
+    sw = SvdWork{};
+    flag = nullptr;
+    status = nullptr;
+    sgn = nullptr;
+    dcap = 0;
+  }
+};
+
+struct ssa_plan_s {
+  int64_t N = 0, L = 0, K = 0, Lw = 0, Kw = 0;
+  bool transposed = false;
+  ssa_opts_t opts{};
+  cudaStream_t stream = nullptr;
+  Geom g{};
+  bool small = false;
+  cplx<df64>* tw = nullptr;
+  cplx<df64>* tA = nullptr;
+  cplx<df64>* tB = nullptr;
+  cplx<df64>* chat = nullptr;
+  void* scratch = nullptr;
+  double* f_dev = nullptr;
+  bool has_series = false;
+  Workspace ws;
+};
+
+struct ssa_decomp_s {
+  ssa_plan_t plan = nullptr;
+  int k = 0, d = 0, converged = 0, restarts = 0;
+  int64_t matvecs = 0;
+  double* sigma = nullptr;  // k
+  double* resid = nullptr;  // k
+  double* U = nullptr;      // L x k (user orientation)
+  double* V = nullptr;      // K x k
+  df64* Uw = nullptr;       // Lw x k (working orientation, for Hankelization)
+  df64* Vw = nullptr;       // Kw x k
+};
+
+extern "C" void ssa_default_opts(ssa_opts_t* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->precision = SSA_PREC_F64;
+  o->tol = 0.0;
+  o->max_restarts = 200;
+  o->krylov_dim = 0;
+  o->keep = 0;
+  o->seed = 0;
+  o->stream = nullptr;
+}
+
+extern "C" const char* ssa_strerror(int code) {
+  switch (code) {
+    case SSA_OK: return "ok";
+    case SSA_EINVAL: return "invalid argument";
+    case SSA_ENOMEM: return "out of device memory";
+    case SSA_ENOCONV: return "Lanczos did not converge within max_restarts";
+    case SSA_ETIMEOUT: return "bounded device wait ran out";
+    case SSA_ECUDA: return "CUDA error";
+    case SSA_ENUMERIC: return "non-finite value";
+    default: return "unknown status";
+  }
+}
+extern "C" const char* ssa_last_error(void) { return g_err; }
+
+extern "C" void ssa_plan_destroy(ssa_plan_t p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->stream);
+  p->ws.release();
+  cudaFree(p->tw);
+  cudaFree(p->tA);
+  cudaFree(p->tB);
+  cudaFree(p->chat);
+  cudaFree(p->scratch);
+  cudaFree(p->f_dev);
+  delete p;
+}
+
+extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_plan_t* out) {
+  REQ(out != nullptr, "out is NULL");
+  *out = nullptr;
+  REQ(N > 2, "need N > 2 (got %lld)", (long long)N);
+  REQ(L > 1 && L < N, "need 1 < L < N (got L=%lld, N=%lld)", (long long)L, (long long)N);
+  REQ(N <= ((int64_t)1 << 23), "N up to 2^23 is supported (got %lld)", (long long)N);
+  ssa_opts_t o;
+  if (opts) o = *opts;
+  else ssa_default_opts(&o);
+  REQ(o.precision == SSA_PREC_F64 || o.precision == SSA_PREC_F32C, "unknown precision %d", o.precision);
+  ssa_plan_s* p = new (std::nothrow) ssa_plan_s();
+  if (!p) return SSA_ENOMEM;
+  p->opts = o;
+  p->stream = reinterpret_cast<cudaStream_t>(o.stream);
+  p->N = N;
+  p->L = L;
+  p->K = N - L + 1;
+  p->transposed = L > p->K;
+  p->Lw = p->transposed ? p->K : L;
+  p->Kw = p->transposed ? L : p->K;
+  int64_t M = 4;
+  while (M < N) M *= 2;
+  Geom& g = p->g;
+  g.N = N;
+  g.L = p->Lw;
+  g.K = p->Kw;
+  g.M = M;
+  g.lg_n = ilog2(M) - 1;
+  g.lg_n1 = g.lg_n / 2;
+  g.lg_n2 = g.lg_n - g.lg_n1;
+  p->small = small_path(g, o.precision);
+  g.lg_P = p->small ? g.lg_n : g.lg_n2;
+  const int64_t P = (int64_t)1 << g.lg_P;
+  const int lgM = ilog2(M);
+  g.tws = (lgM + 1) / 2;
+  const int64_t nA = M >> g.tws, nB = (int64_t)1 << g.tws;
+  std::vector<cplx<df64>> htw(P), hA(nA), hB(nB);
+  for (int64_t m = 0; m < P; ++m) htw[m] = tw_entry(m, P);
+  for (int64_t m = 0; m < nA; ++m) hA[m] = tw_entry(m << g.tws, M);
+  for (int64_t m = 0; m < nB; ++m) hB[m] = tw_entry(m, M);
+  auto fail = [&](int code) {
+    ssa_plan_destroy(p);
+    return code;
+  };
+  const int64_t n = (int64_t)1 << g.lg_n;
+#define PK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) {                    \
+      set_err("%s: %s", #x, cudaGetErrorString(e_)); \
+      return fail(e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA); \
+    }                                           \
+  } while (0)
+  PK(cudaMalloc(&p->tw, P * sizeof(cplx<df64>)));
+  PK(cudaMalloc(&p->tA, nA * sizeof(cplx<df64>)));
+  PK(cudaMalloc(&p->tB, nB * sizeof(cplx<df64>)));
+  PK(cudaMalloc(&p->chat, (n + 1) * sizeof(cplx<df64>)));
+  PK(cudaMalloc(&p->scratch, spectral_scratch_bytes(g)));
+  PK(cudaMalloc(&p->f_dev, N * sizeof(double)));
+  PK(cudaMemcpy(p->tw, htw.data(), P * sizeof(cplx<df64>), cudaMemcpyHostToDevice));
+  PK(cudaMemcpy(p->tA, hA.data(), nA * sizeof(cplx<df64>), cudaMemcpyHostToDevice));
+  PK(cudaMemcpy(p->tB, hB.data(), nB * sizeof(cplx<df64>), cudaMemcpyHostToDevice));
+#undef PK
+  g.tw = p->tw;
+  g.tA = p->tA;
+  g.tB = p->tB;
+  *out = p;
+  return SSA_OK;
+}
+
+extern "C" int ssa_plan_info(ssa_plan_t p, int64_t* M, int* single_cta) {
+  REQ(p != nullptr, "plan is NULL");
+  if (M) *M = p->g.M;
+  if (single_cta) *single_cta = p->small ? 1 : 0;
+  return SSA_OK;
+}
+
+static int set_series(ssa_plan_t p, const double* f) {
+  if (is_device_ptr(f)) {
+    CK(cudaMemcpyAsync(p->f_dev, f, p->N * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  } else {
+    for (int64_t i = 0; i < p->N; ++i)
+      if (!std::isfinite(f[i])) {
+        set_err("f[%lld] is not finite", (long long)i);
+        return SSA_ENUMERIC;
+      }
+    CK(cudaMemcpyAsync(p->f_dev, f, p->N * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  }
+  const float scale = 1.0f / (4.0f * (float)((int64_t)1 << p->g.lg_n));
+  launch_spectrum(p->g, p->f_dev, p->chat, p->small ? 1 : 0, scale, p->scratch, p->stream);
+  CHECK_LAUNCH();
+  p->has_series = true;
+  return SSA_OK;
+}
+
+extern "C" int ssa_set_series(ssa_plan_t p, const double* f) {
+  REQ(p != nullptr && f != nullptr, "plan or f is NULL");
+  int rc = set_series(p, f);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(p->stream));
+  return SSA_OK;
+}
+
+extern "C" int ssa_get_spectrum(ssa_plan_t p, double* re, double* im) {
+  REQ(p != nullptr && re != nullptr && im != nullptr, "NULL argument");
+  REQ(p->has_series, "no series set");
+  const int64_t n = (int64_t)1 << p->g.lg_n;
+  std::vector<cplx<df64>> h(n + 1);
+  CK(cudaMemcpyAsync(h.data(), p->chat, (n + 1) * sizeof(cplx<df64>), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  const double unscale = 4.0 * (double)n;
+  std::vector<double> hre(n + 1), him(n + 1);
+  const int64_t n1 = (int64_t)1 << p->g.lg_n1, n2 = (int64_t)1 << p->g.lg_n2;
+  for (int64_t k = 0; k <= n; ++k) {
+    int64_t pos = k;
+    if (!p->small && k < n) {
+      const int64_t c = k % n1, e = k / n1;
+      pos = c * n2 + e;
+    }
+    hre[k] = df_to_double(h[pos].re) * unscale;
+    him[k] = df_to_double(h[pos].im) * unscale;
+  }
+  const bool dre = is_device_ptr(re), dim_ = is_device_ptr(im);
+  if (dre) CK(cudaMemcpy(re, hre.data(), (n + 1) * sizeof(double), cudaMemcpyHostToDevice));
+  else std::memcpy(re, hre.data(), (n + 1) * sizeof(double));
+  if (dim_) CK(cudaMemcpy(im, him.data(), (n + 1) * sizeof(double), cudaMemcpyHostToDevice));
+  else std::memcpy(im, him.data(), (n + 1) * sizeof(double));
+  return SSA_OK;
+}
+
+extern "C" int ssa_matvec(ssa_plan_t p, int transpose, const double* x, double* y, int nvec) {
+  REQ(p != nullptr && x != nullptr && y != nullptr, "NULL argument");
+  REQ(nvec >= 1, "nvec must be >= 1");
+  REQ(p->has_series, "no series set (ssa_set_series)");
+  const int t = (transpose ? 1 : 0) ^ (p->transposed ? 1 : 0);
+  const int64_t in_len = t ? p->Lw : p->Kw, out_len = t ? p->Kw : p->Lw;
+  Staged<double> xs, ys;
+  int rc = xs.in(x, (size_t)in_len * nvec, p->stream);
+  if (rc) return rc;
+  rc = ys.out(y, (size_t)out_len * nvec, p->stream);
+  if (rc) return rc;
+  void* scratch = p->scratch;
+  void* tmp = nullptr;
+  if (!p->small && nvec > 1) {
+    CK(cudaMallocAsync(&tmp, ((size_t)1 << p->g.lg_n) * sizeof(cplx<df64>) * nvec, p->stream));
+    scratch = tmp;
+  }
+  launch_matvec_d(p->g, p->opts.precision, t, xs.dev, in_len, ys.dev, out_len, nvec, p->chat, scratch, p->stream);
+  CHECK_LAUNCH();
+  if (tmp) CK(cudaFreeAsync(tmp, p->stream));
+  rc = ys.finish();
+  if (rc) return rc;
+  if (ys.needs_sync() || xs.owned) CK(cudaStreamSynchronize(p->stream));
+  return SSA_OK;
+}
+
+// ------------------------------------------------------------------ Lanczos
+static int ensure_workspace(ssa_plan_t p, int d) {
+  Workspace& w = p->ws;
+  if (w.dcap >= d) return SSA_OK;
+  w.release();
+  const int cols = d + 2;
+  w.ldu = (p->Lw + 3) / 4 * 4;
+  w.ldv = (p->Kw + 3) / 4 * 4;
+  w.ldb = d + 2;
+  const int64_t dimmax = p->Kw > p->Lw ? p->Kw : p->Lw;
+  const int G = reorth_blocks(dimmax);
+  for (int i = 0; i < 2; ++i) {
+    CK(cudaMalloc(&w.Ub[i], (size_t)w.ldu * cols * sizeof(df64)));
+    CK(cudaMalloc(&w.Vb[i], (size_t)w.ldv * cols * sizeof(df64)));
+    CK(cudaMemset(w.Ub[i], 0, (size_t)w.ldu * cols * sizeof(df64)));
+    CK(cudaMemset(w.Vb[i], 0, (size_t)w.ldv * cols * sizeof(df64)));
+  }
+  CK(cudaMalloc(&w.B, (size_t)w.ldb * w.ldb * sizeof(df64)));
+  CK(cudaMalloc(&w.y, (size_t)((dimmax + 3) / 4 * 4) * sizeof(df64)));
+  w.rw.ldp = MAXCOL + 1;
+  CK(cudaMalloc(&w.rw.part, (size_t)G * w.rw.ldp * sizeof(df64)));
+  CK(cudaMalloc(&w.rw.h, (MAXCOL + 1) * sizeof(df64)));
+  CK(cudaMalloc(&w.rw.nrm, sizeof(df64)));
+  CK(cudaMalloc(&w.rw.counter, sizeof(int)));
+  CK(cudaMemset(w.rw.counter, 0, sizeof(int)));
+  const size_t sq = (size_t)cols * cols * sizeof(df64);
+  CK(cudaMalloc(&w.sw.A, sq));
+  CK(cudaMalloc(&w.sw.W, sq));
+  CK(cudaMalloc(&w.sw.P, sq));
+  CK(cudaMalloc(&w.sw.Q, sq));
+  CK(cudaMalloc(&w.sw.sigma, cols * sizeof(df64)));
+  CK(cudaMalloc(&w.sw.resid, cols * sizeof(double)));
+  CK(cudaMalloc(&w.sw.sigma_d, cols * sizeof(double)));
+  CK(cudaMalloc(&w.sw.conv, sizeof(int)));
+  CK(cudaMalloc(&w.est, sizeof(df64)));
+  CK(cudaMalloc(&w.dummy, sizeof(df64)));
+  CK(cudaMalloc(&w.flag, sizeof(int)));
+  CK(cudaMalloc(&w.status, sizeof(unsigned)));
+  CK(cudaMalloc(&w.sgn, cols * sizeof(int)));
+  w.dcap = d;
+  return SSA_OK;
+}
+
+// Round-robin (circle method) schedule: cc-1 rounds of cc/2 disjoint pairs.
+static int get_schedule(Workspace& w, int c, const int2** out) {
+  auto it = w.sched.find(c);
+  if (it != w.sched.end()) {
+    *out = it->second;
+    return SSA_OK;
+  }
+  const int cc = c + (c & 1);
+  std::vector<int> pos(cc);
+  for (int i = 0; i < cc; ++i) pos[i] = i;
+  std::vector<int2> h;
+  h.reserve((size_t)(cc - 1) * (cc / 2));
+  for (int rnd = 0; rnd < cc - 1; ++rnd) {
+    for (int j = 0; j < cc / 2; ++j) h.push_back(make_int2(pos[j], pos[cc - 1 - j]));
+    const int last = pos[cc - 1];
+    for (int i = cc - 1; i >= 2; --i) pos[i] = pos[i - 1];
+    if (cc > 1) pos[1] = last;
+  }
+  int2* d = nullptr;
+  if (!h.empty()) {
+    CK(cudaMalloc(&d, h.size() * sizeof(int2)));
+    CK(cudaMemcpy(d, h.data(), h.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  }
+  w.sched[c] = d;
+  *out = d;
+  return SSA_OK;
+}
+
+static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
+  const int prec = p->opts.precision;
+  const int64_t Lw = p->Lw, Kw = p->Kw;
+  const int64_t mn = Lw < Kw ? Lw : Kw;
+  int d = p->opts.krylov_dim > 0 ? p->opts.krylov_dim : (2 * k > k + 32 ? 2 * k : k + 32);
+  if (d > mn) d = (int)mn;
+  if (d < k) d = k;
+  REQ(d <= MAXCOL - 2, "Krylov dimension %d exceeds %d", d, MAXCOL - 2);
+  int kk = p->opts.keep > 0 ? p->opts.keep : k + (d - k + 1) / 2;
+  if (kk > d - 1) kk = d - 1;
+  if (kk < k) kk = k;
+  double tol = p->opts.tol;
+  if (!(tol > 0)) tol = prec == SSA_PREC_F32C ? 1e-7 * std::sqrt((double)ilog2(p->g.M)) : 1e-13;
+  int rc = ensure_workspace(p, d);
+  if (rc) return rc;
+  Workspace& w = p->ws;
+  cudaStream_t s = p->stream;
+  int cur = 0;
+  df64* U = w.Ub[cur];
+  df64* V = w.Vb[cur];
+  CK(cudaMemsetAsync(w.B, 0, (size_t)w.ldb * w.ldb * sizeof(df64), s));
+  CK(cudaMemsetAsync(w.est, 0, sizeof(df64), s));
+  CK(cudaMemsetAsync(w.flag, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(w.status, 0, sizeof(unsigned), s));
+  w.sw.max_sweeps = 60;
+  w.sw.rot_tol = 1e-13f;
+  const uint64_t seed = p->opts.seed;
+  uint64_t stream_id = 0;
+  int64_t matvecs = 0;
+  // p_0 (Algorithm 1, line 1): seeded uniform(-1, 1), normalised into u_1
+  launch_random_fill(w.y, Lw, seed, stream_id++, s);
+  launch_cgs2(U, w.ldu, 0, w.y, Lw, w.rw, nullptr, s);
+  launch_normalize(w.y, Lw, w.rw, U, w.dummy, w.est, w.flag, 0, seed, stream_id++, w.status, s);
+  CHECK_LAUNCH();
+  int r = 1, c = 0;
+  auto side = [&](bool vside) -> int {
+    // v-side: alpha v_{c+1} = X^T u_r - ... ; u-side: beta u_{r+1} = X v_c - ...
+    df64* Qb = vside ? V : U;
+    const int64_t ldq = vside ? w.ldv : w.ldu;
+    const int64_t dim = vside ? Kw : Lw;
+    const int ncols = vside ? c : r;
+    const df64* src = vside ? U + (int64_t)(r - 1) * w.ldu : V + (int64_t)(c - 1) * w.ldv;
+    df64* bentry = vside ? w.B + (int64_t)(r - 1) * w.ldb + c : w.B + (int64_t)r * w.ldb + (c - 1);
+    launch_matvec_df(p->g, prec, vside ? 1 : 0, src, 0, w.y, 0, 1, p->chat, p->scratch, s);
+    ++matvecs;
+    launch_cgs2(Qb, ldq, ncols, w.y, dim, w.rw, nullptr, s);
+    df64* qcol = Qb + (int64_t)ncols * ldq;
+    launch_normalize(w.y, dim, w.rw, qcol, bentry, w.est, w.flag, 0, seed, stream_id, w.status, s);
+    launch_cgs2(Qb, ldq, ncols, w.y, dim, w.rw, w.flag, s);
+    launch_normalize(w.y, dim, w.rw, qcol, bentry, w.est, w.flag, 1, seed, stream_id, w.status, s);
+    ++stream_id;
+    CHECK_LAUNCH();
+    if (vside) ++c;
+    else ++r;
+    return SSA_OK;
+  };
+  int restarts = 0, converged = 0;
+  rc = side(true);
+  if (rc) return rc;
+  unsigned status = 0;
+  for (;;) {
+    while (c < d + 1) {
+      rc = side(false);
+      if (rc) return rc;
+      rc = side(true);
+      if (rc) return rc;
+    }
+    const int cp = c - 1;
+    const int2* sched = nullptr;
+    rc = get_schedule(w, cp, &sched);
+    if (rc) return rc;
+    launch_small_svd(w.B, w.ldb, r, cp, sched, w.sw, k, tol, w.est, w.status, s);
+    CHECK_LAUNCH();
+    CK(cudaMemcpyAsync(&converged, w.sw.conv, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&status, w.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (status & SSA_DEV_NONFINITE) {
+      set_err("non-finite value in the Lanczos recurrence");
+      return SSA_ENUMERIC;
+    }
+    if (converged || restarts >= p->opts.max_restarts || kk >= cp) break;
+    // thick restart: U <- U P[:, :kk], V <- [V Q[:, :kk], v_{c}], B <- [diag | rho]
+    const int nxt = cur ^ 1;
+    launch_ritz(U, w.ldu, r, w.sw.P, r, kk, w.Ub[nxt], w.ldu, Lw, s);
+    launch_ritz(V, w.ldv, cp, w.sw.Q, cp, kk, w.Vb[nxt], w.ldv, Kw, s);
+    launch_copy_df(V + (int64_t)cp * w.ldv, w.Vb[nxt] + (int64_t)kk * w.ldv, Kw, s);
+    launch_restart_B(w.B, w.ldb, w.ldb, w.sw, r, kk, cp, s);
+    CHECK_LAUNCH();
+    cur = nxt;
+    U = w.Ub[cur];
+    V = w.Vb[cur];
+    r = kk;
+    c = kk + 1;
+    ++restarts;
+  }
+  // Ritz vectors for the k wanted triples
+  const int nxt = cur ^ 1;
+  df64* Uf = w.Ub[nxt];
+  df64* Vf = w.Vb[nxt];
+  const int cp = c - 1;
+  launch_ritz(U, w.ldu, r, w.sw.P, r, k, Uf, w.ldu, Lw, s);
+  launch_ritz(V, w.ldv, cp, w.sw.Q, cp, k, Vf, w.ldv, Kw, s);
+  CHECK_LAUNCH();
+  // sign rule on the user's left vectors
+  const df64* Uuser = p->transposed ? Vf : Uf;
+  const int64_t lduser = p->transposed ? w.ldv : w.ldu;
+  const int64_t Luser = p->transposed ? Kw : Lw;
+  launch_sign(Uuser, lduser, Luser, k, w.sgn, s);
+  launch_store_cols(Uf, w.ldu, Lw, k, w.sgn, p->transposed ? res->V : res->U, Lw, s);
+  launch_store_cols(Vf, w.ldv, Kw, k, w.sgn, p->transposed ? res->U : res->V, Kw, s);
+  // working-orientation copies for Hankelization
+  CK(cudaMemcpy2DAsync(res->Uw, Lw * sizeof(df64), Uf, w.ldu * sizeof(df64), Lw * sizeof(df64), k,
+                       cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpy2DAsync(res->Vw, Kw * sizeof(df64), Vf, w.ldv * sizeof(df64), Kw * sizeof(df64), k,
+                       cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(res->sigma, w.sw.sigma_d, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(res->resid, w.sw.resid, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CHECK_LAUNCH();
+  CK(cudaStreamSynchronize(s));
+  res->k = k;
+  res->d = d;
+  res->converged = converged;
+  res->restarts = restarts;
+  res->matvecs = matvecs;
+  // Uw / Vw keep the unsigned vectors: Hankelizing sigma u v^T does not
+  // depend on flipping u and v together.
+  return converged ? SSA_OK : SSA_ENOCONV;
+}
+
+extern "C" void ssa_decomp_destroy(ssa_decomp_t d) {
+  if (!d) return;
+  cudaFree(d->sigma);
+  cudaFree(d->resid);
+  cudaFree(d->U);
+  cudaFree(d->V);
+  cudaFree(d->Uw);
+  cudaFree(d->Vw);
+  delete d;
+}
+
+extern "C" int ssa_decompose(ssa_plan_t p, const double* f, int k, ssa_decomp_t* out) {
+  REQ(p != nullptr && out != nullptr, "NULL argument");
+  *out = nullptr;
+  const int64_t mn = p->Lw;
+  REQ(k >= 1 && k <= mn, "need 1 <= k <= min(L, K) = %lld (got %d)", (long long)mn, k);
+  if (f) {
+    int rc = set_series(p, f);
+    if (rc) return rc;
+  }
+  REQ(p->has_series, "no series given");
+  ssa_decomp_s* d = new (std::nothrow) ssa_decomp_s();
+  if (!d) return SSA_ENOMEM;
+  d->plan = p;
+#define DK(x)                                       \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) {                        \
+      set_err("%s: %s", #x, cudaGetErrorString(e_)); \
+      ssa_decomp_destroy(d);                        \
+      return e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA; \
+    }                                               \
+  } while (0)
+  DK(cudaMalloc(&d->sigma, k * sizeof(double)));
+  DK(cudaMalloc(&d->resid, k * sizeof(double)));
+  DK(cudaMalloc(&d->U, (size_t)p->L * k * sizeof(double)));
+  DK(cudaMalloc(&d->V, (size_t)p->K * k * sizeof(double)));
+  DK(cudaMalloc(&d->Uw, (size_t)p->Lw * k * sizeof(df64)));
+  DK(cudaMalloc(&d->Vw, (size_t)p->Kw * k * sizeof(df64)));
+#undef DK
+  int rc = lanczos(p, k, d);
+  if (rc != SSA_OK && rc != SSA_ENOCONV) {
+    ssa_decomp_destroy(d);
+    return rc;
+  }
+  *out = d;
+  return rc;
+}
+
+extern "C" int ssa_decomp_info(ssa_decomp_t d, int* k, int* converged, int* restarts, int64_t* matvecs,
+                               int* krylov_dim) {
+  REQ(d != nullptr, "decomposition is NULL");
+  if (k) *k = d->k;
+  if (converged) *converged = d->converged;
+  if (restarts) *restarts = d->restarts;
+  if (matvecs) *matvecs = d->matvecs;
+  if (krylov_dim) *krylov_dim = d->d;
+  return SSA_OK;
+}
+
+extern "C" int ssa_decomp_get(ssa_decomp_t d, double* sigma, double* U, double* V, double* resid) {
+  REQ(d != nullptr, "decomposition is NULL");
+  const ssa_plan_t p = d->plan;
+  cudaStream_t s = p->stream;
+  if (sigma) CK(cudaMemcpyAsync(sigma, d->sigma, d->k * sizeof(double), cudaMemcpyDefault, s));
+  if (resid) CK(cudaMemcpyAsync(resid, d->resid, d->k * sizeof(double), cudaMemcpyDefault, s));
+  if (U) CK(cudaMemcpyAsync(U, d->U, (size_t)p->L * d->k * sizeof(double), cudaMemcpyDefault, s));
+  if (V) CK(cudaMemcpyAsync(V, d->V, (size_t)p->K * d->k * sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  return SSA_OK;
+}
+
+// validate CSR groups (host copies); indices in [0, r), disjoint
+static int check_groups(const int32_t* off, const int32_t* idx, int m, int r, std::vector<int32_t>& hoff,
+                        std::vector<int32_t>& hidx) {
+  REQ(m >= 1, "need m >= 1 groups");
+  REQ(off != nullptr && idx != nullptr, "NULL group arrays");
+  hoff.resize(m + 1);
+  if (is_device_ptr(off)) CK(cudaMemcpy(hoff.data(), off, (m + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  else std::memcpy(hoff.data(), off, (m + 1) * sizeof(int32_t));
+  REQ(hoff[0] == 0, "grp_off[0] must be 0");
+  for (int g = 0; g < m; ++g) REQ(hoff[g + 1] >= hoff[g], "grp_off must be non-decreasing");
+  const int nidx = hoff[m];
+  hidx.resize(nidx > 0 ? nidx : 1);
+  if (nidx > 0) {
+    if (is_device_ptr(idx)) CK(cudaMemcpy(hidx.data(), idx, nidx * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    else std::memcpy(hidx.data(), idx, nidx * sizeof(int32_t));
+  }
+  std::vector<char> seen(r, 0);
+  for (int i = 0; i < nidx; ++i) {
+    REQ(hidx[i] >= 0 && hidx[i] < r, "group index %d out of range [0, %d)", hidx[i], r);
+    REQ(!seen[hidx[i]], "index %d appears in two groups", hidx[i]);
+    seen[hidx[i]] = 1;
+  }
+  return SSA_OK;
+}
+
+static int hankel_common(ssa_plan_t p, const double* sigma_dev, const df64* Uw, int64_t ldu, const df64* Vw,
+                         int64_t ldv, int r, const int32_t* grp_off, const int32_t* grp_idx, int m, double* out) {
+  std::vector<int32_t> hoff, hidx;
+  int rc = check_groups(grp_off, grp_idx, m, r, hoff, hidx);
+  if (rc) return rc;
+  cudaStream_t s = p->stream;
+  int32_t *doff = nullptr, *didx = nullptr;
+  CK(cudaMallocAsync(&doff, (m + 1) * sizeof(int32_t), s));
+  CK(cudaMallocAsync(&didx, hidx.size() * sizeof(int32_t), s));
+  CK(cudaMemcpyAsync(doff, hoff.data(), (m + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(didx, hidx.data(), hidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  Staged<double> os;
+  rc = os.out(out, (size_t)m * p->N, s);
+  if (rc) return rc;
+  launch_hankel(p->g, p->opts.precision, Uw, ldu, Vw, ldv, sigma_dev, doff, didx, hoff.data(), hidx.data(), m,
+                os.dev, p->N, p->scratch, s);
+  CHECK_LAUNCH();
+  rc = os.finish();
+  if (rc) return rc;
+  CK(cudaFreeAsync(doff, s));
+  CK(cudaFreeAsync(didx, s));
+  // host group arrays must outlive the enqueue of the large-M path (done) and
+  // the copies above; synchronise so hoff/hidx can be released safely
+  CK(cudaStreamSynchronize(s));
+  return SSA_OK;
+}
+
+extern "C" int ssa_reconstruct(ssa_decomp_t d, const int32_t* grp_off, const int32_t* grp_idx, int m, double* out) {
+  REQ(d != nullptr && out != nullptr, "NULL argument");
+  ssa_plan_t p = d->plan;
+  return hankel_common(p, d->sigma, d->Uw, p->Lw, d->Vw, p->Kw, d->k, grp_off, grp_idx, m, out);
+}
+
+extern "C" int ssa_hankelize(ssa_plan_t p, const double* sigma, const double* U, int64_t ldu, const double* V,
+                             int64_t ldv, int r, const int32_t* grp_off, const int32_t* grp_idx, int m, double* out) {
+  REQ(p != nullptr && sigma != nullptr && U != nullptr && V != nullptr && out != nullptr, "NULL argument");
+  REQ(r >= 1, "need r >= 1");
+  REQ(ldu >= p->L && ldv >= p->K, "leading dimensions too small");
+  cudaStream_t s = p->stream;
+  Staged<double> ss, us, vs;
+  int rc = ss.in(sigma, r, s);
+  if (rc) return rc;
+  rc = us.in(U, (size_t)ldu * (r - 1) + p->L, s);
+  if (rc) return rc;
+  rc = vs.in(V, (size_t)ldv * (r - 1) + p->K, s);
+  if (rc) return rc;
+  df64 *Uw = nullptr, *Vw = nullptr;
+  CK(cudaMallocAsync(&Uw, (size_t)p->Lw * r * sizeof(df64), s));
+  CK(cudaMallocAsync(&Vw, (size_t)p->Kw * r * sizeof(df64), s));
+  // working orientation: X^T's left vectors are the user's V when L > K
+  const double* uw_src = p->transposed ? vs.dev : us.dev;
+  const double* vw_src = p->transposed ? us.dev : vs.dev;
+  launch_double_to_df(uw_src, p->transposed ? ldv : ldu, Uw, p->Lw, p->Lw, r, s);
+  launch_double_to_df(vw_src, p->transposed ? ldu : ldv, Vw, p->Kw, p->Kw, r, s);
+  CHECK_LAUNCH();
+  rc = hankel_common(p, ss.dev, Uw, p->Lw, Vw, p->Kw, r, grp_off, grp_idx, m, out);
+  cudaFreeAsync(Uw, s);
+  cudaFreeAsync(Vw, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  return SSA_OK;
+}

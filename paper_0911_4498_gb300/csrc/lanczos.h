@@ -1,0 +1,50 @@
+// Host-side interface of the Lanczos engine kernels (lanczos_kernels.cu).
+#pragma once
+#include "common.cuh"
+
+namespace ssa {
+
+constexpr int RT = 256;              // threads per reorthogonalisation block
+constexpr int RP = 4;                // row pairs per thread
+constexpr int SLAB = 2 * RT * RP;    // rows per block
+constexpr int MAXCOL = 512;          // largest basis size (Krylov dimension + 1)
+constexpr int SVD_THREADS = 512;
+
+struct ReorthWork {
+  df64* part;    // [blocks][ldp] partial sums
+  int ldp;
+  df64* h;       // projection coefficients (MAXCOL + 1)
+  df64* nrm;     // squared norm after the last update
+  int* counter;  // last-block counter (returns to 0 after each kernel)
+};
+
+struct SvdWork {
+  df64 *A, *W;            // Jacobi work: r x c and c x c (column-major)
+  df64 *sigma, *P, *Q;    // sorted outputs
+  double *resid, *sigma_d;
+  int* conv;
+  int max_sweeps;
+  float rot_tol;
+};
+
+int reorth_blocks(int64_t dim);
+void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, const int* flag,
+                 cudaStream_t s);
+void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est, int* flag, int mode,
+                      uint64_t seed, uint64_t stream, unsigned* status, cudaStream_t s);
+void launch_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stream, cudaStream_t s);
+void launch_small_svd(const df64* B, int ldb, int r, int c, const int2* sched, SvdWork& sw, int k, double tol_conv,
+                      df64* est, unsigned* status, cudaStream_t s);
+void launch_restart_B(df64* B, int ldb, int nrows_clear, const SvdWork& sw, int r, int kk, int c_old,
+                      cudaStream_t s);
+void launch_ritz(const df64* Q, int64_t ldq, int r, const df64* P, int ldp, int ncol, df64* out, int64_t ldo,
+                 int64_t dim, cudaStream_t s);
+void launch_copy_df(const df64* src, df64* dst, int64_t n, cudaStream_t s);
+void launch_sign(const df64* U, int64_t ldu, int64_t dim, int k, int* sgn, cudaStream_t s);
+void launch_store_cols(const df64* src, int64_t lds, int64_t dim, int ncol, const int* sgn, double* dst, int64_t ldd,
+                       cudaStream_t s);
+void launch_df_to_double(const df64* src, double* dst, int64_t n, cudaStream_t s);
+void launch_double_to_df(const double* src, int64_t lds, df64* dst, int64_t ldd, int64_t dim, int ncol,
+                         cudaStream_t s);
+
+}  // namespace ssa

@@ -1,0 +1,566 @@
+// FFT-based trajectory-matrix products (Algorithms 2 and 3), the cached
+// spectrum of the series (Algorithm 2 steps 1-2) and grouped rank-1
+// Hankelization (Algorithm 4), for one CTA per transform (M <= 16384 in
+// double-float, M <= 32768 in FP32) or a four-step decomposition over three
+// kernels for large M.
+//
+// Index conventions (0-based; the series f[0..N-1] is the paper's f_1..f_N):
+//   M >= N is the FFT length (a power of two), n = M/2 complex points.
+//   c_j = f[N-L+j] for j < L, 0 for L <= j < L+M-N, f[j-L-(M-N)] beyond
+//   (Algorithm 2 step 1 with M-N zeros between its two blocks, so every
+//   M >= N embeds the same Toeplitz matrix);
+//   X v  : w_j = v[K-1-j] (j < K), output p_0..p_{L-1}       (Algorithm 2)
+//   X^T u: w_j = u[M-1-j] (j >= M-L), output p_{M-K}..p_{M-1} (Algorithm 3,
+//          the printed slice p'_{L-1}..p'_N has one entry too many).
+//   Hankelization: u' = (u, 0...), v' = (v, 0...) of length M >= L+K-1, the
+//   linear convolution by FFT, divided by the antidiagonal counts
+//   min(t+1, L, K, N-t) (Algorithm 4 prints a product with the counts; the
+//   convolution identity of section 5 requires the quotient).
+#include <cstdio>
+#include <mutex>
+#include <unordered_map>
+#include "spectral.h"
+#include "fft.cuh"
+
+namespace ssa {
+
+// ---------------------------------------------------------------- loaders
+template <class T> SSA_D T ld(const df64* p, int64_t i) { return scal<T>::from_df(p[i]); }
+template <class T> SSA_D T ld(const double* p, int64_t i) { return scal<T>::from_double(__ldg(p + i)); }
+SSA_D void st(df64* p, int64_t i, float v) { p[i] = make_df(v, 0.f); }
+SSA_D void st(df64* p, int64_t i, df64 v) { p[i] = v; }
+SSA_D void st(double* p, int64_t i, float v) { p[i] = (double)v; }
+SSA_D void st(double* p, int64_t i, df64 v) { p[i] = df_to_double(v); }
+
+template <class T, int G, class In>
+SSA_D T gather(const Geom& g, const In* x, int64_t glen, int64_t j) {
+  if (G == GATHER_X) return j < g.K ? ld<T>(x, g.K - 1 - j) : scal<T>::zero();
+  if (G == GATHER_XT) return j >= g.M - g.L ? ld<T>(x, g.M - 1 - j) : scal<T>::zero();
+  if (G == GATHER_CIRC) {
+    if (j < g.L) return ld<T>(x, g.N - g.L + j);
+    const int64_t j0 = g.L + (g.M - g.N);
+    return j >= j0 ? ld<T>(x, j - j0) : scal<T>::zero();
+  }
+  return j < glen ? ld<T>(x, j) : scal<T>::zero();  // GATHER_PAD
+}
+
+template <class T> SSA_D cplx<T> c_one() { return mk(scal<T>::from_double(1.0), scal<T>::zero()); }
+
+SSA_D float cnt_recip_f(const Geom& g, int64_t t) {
+  int64_t c = t + 1;
+  if (g.N - t < c) c = g.N - t;
+  const int64_t mn = g.L < g.K ? g.L : g.K;
+  if (mn < c) c = mn;
+  return (float)c;
+}
+template <class T> SSA_D T div_count(T v, float cnt);
+template <> SSA_D float div_count<float>(float v, float cnt) { return v / cnt; }
+template <> SSA_D df64 div_count<df64>(df64 v, float cnt) { return df_div(v, make_df(cnt, 0.f)); }
+template <class T> SSA_D T mul_scalar(T v, float s);
+template <> SSA_D float mul_scalar<float>(float v, float s) { return v * s; }
+template <> SSA_D df64 mul_scalar<df64>(df64 v, float s) { return df_mul_f(v, s); }
+
+// ------------------------------------------------ single-CTA kernels
+// Fused X v / X^T u: gather -> FFT -> real post-process -> x c-hat ->
+// inverse pre-process -> inverse FFT -> window slice.  One CTA per vector.
+template <class T, int THREADS, int MAXE, int G, class In, class Out>
+__global__ void __launch_bounds__(THREADS) k_matvec_small(Geom g, const In* __restrict__ x, int64_t ldx,
+                                                          Out* __restrict__ y, int64_t ldy,
+                                                          const cplx<df64>* __restrict__ chat,
+                                                          int64_t out_off, int64_t out_cnt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int n = 1 << g.lg_n;
+  x += (int64_t)blockIdx.x * ldx;
+  y += (int64_t)blockIdx.x * ldy;
+  for (int t = threadIdx.x; t < n; t += THREADS)
+    buf[t] = mk(gather<T, G>(g, x, 0, 2 * (int64_t)t), gather<T, G>(g, x, 0, 2 * (int64_t)t + 1));
+  __syncthreads();
+  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n, 1, g.tw, g.lg_P);
+  for (int k = threadIdx.x; k <= n / 2; k += THREADS) {
+    const int nk = (n - k) & (n - 1);
+    cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, k) : c_one<T>();
+    cplx<T> wk, wnk, zk, znk;
+    rfft_post(buf[k], buf[nk], tw, wk, wnk);
+    cplx<T> pk = mul_spec(wk, chat[k]);
+    cplx<T> pnk = mul_spec(wnk, chat[n - k]);
+    irfft_pre(pk, pnk, tw, zk, znk);
+    buf[k] = zk;
+    if (k != 0 && nk != k) buf[nk] = znk;
+  }
+  __syncthreads();
+  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n, 1, g.tw, g.lg_P);
+  for (int64_t m = threadIdx.x; m < out_cnt; m += THREADS) {
+    const int64_t i = out_off + m;
+    const cplx<T> z = buf[i >> 1];
+    st(y, m, (i & 1) ? z.im : z.re);
+  }
+}
+
+// Half spectrum W_0..W_n of a real length-M input (natural order), times scale.
+template <class T, int THREADS, int MAXE, int G, class In>
+__global__ void __launch_bounds__(THREADS) k_rfft_small(Geom g, const In* __restrict__ x, int64_t ldx, int64_t glen,
+                                                        cplx<df64>* __restrict__ out, int64_t ldo, float scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int n = 1 << g.lg_n;
+  x += (int64_t)blockIdx.x * ldx;
+  out += (int64_t)blockIdx.x * ldo;
+  for (int t = threadIdx.x; t < n; t += THREADS)
+    buf[t] = mk(gather<T, G>(g, x, glen, 2 * (int64_t)t), gather<T, G>(g, x, glen, 2 * (int64_t)t + 1));
+  __syncthreads();
+  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n, 1, g.tw, g.lg_P);
+  const float s = 0.5f * scale;
+  for (int k = threadIdx.x; k <= n / 2; k += THREADS) {
+    const int nk = (n - k) & (n - 1);
+    cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, k) : c_one<T>();
+    cplx<T> wk, wnk;
+    rfft_post(buf[k], buf[nk], tw, wk, wnk);
+    wk = c_scale(wk, s);
+    wnk = c_scale(wnk, s);
+    out[k] = mk(scal<T>::to_df(wk.re), scal<T>::to_df(wk.im));
+    out[n - k] = mk(scal<T>::to_df(wnk.re), scal<T>::to_df(wnk.im));
+  }
+}
+
+// Grouped rank-1 Hankelization (Algorithm 4 summed over a group): one CTA per
+// group; u'_i and v'_i are transformed together (two length-n FFTs), the
+// products sigma_i U_k V_k accumulate in registers, then one inverse FFT and
+// the division by the antidiagonal counts.
+template <class T, int THREADS, int MAXE, class Out>
+__global__ void __launch_bounds__(THREADS) k_hankel_small(Geom g, const df64* __restrict__ U, int64_t ldu,
+                                                          const df64* __restrict__ V, int64_t ldv,
+                                                          const double* __restrict__ sigma,
+                                                          const int* __restrict__ grp_off,
+                                                          const int* __restrict__ grp_idx,
+                                                          Out* __restrict__ out, int64_t ldo) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* bu = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int n = 1 << g.lg_n;
+  cplx<T>* bv = bu + n;
+  constexpr int MAXK = (MAXE / 4 + 1 + THREADS - 1) / THREADS;
+  cplx<T> acc_k[MAXK], acc_nk[MAXK];
+#pragma unroll
+  for (int q = 0; q < MAXK; ++q) {
+    acc_k[q] = mk(scal<T>::zero(), scal<T>::zero());
+    acc_nk[q] = acc_k[q];
+  }
+  const int grp = blockIdx.x;
+  const int i0 = grp_off[grp], i1 = grp_off[grp + 1];
+  out += (int64_t)grp * ldo;
+  for (int ii = i0; ii < i1; ++ii) {
+    const int comp = grp_idx[ii];
+    const df64* u = U + (int64_t)comp * ldu;
+    const df64* v = V + (int64_t)comp * ldv;
+    for (int t = threadIdx.x; t < n; t += THREADS) {
+      const int64_t j = 2 * (int64_t)t;
+      bu[t] = mk(gather<T, GATHER_PAD>(g, u, g.L, j), gather<T, GATHER_PAD>(g, u, g.L, j + 1));
+      bv[t] = mk(gather<T, GATHER_PAD>(g, v, g.K, j), gather<T, GATHER_PAD>(g, v, g.K, j + 1));
+    }
+    __syncthreads();
+    cta_fft<T, THREADS, MAXE, false>(bu, g.lg_n, 2, g.tw, g.lg_P);
+    const T sg = scal<T>::from_double(sigma[comp]);
+#pragma unroll
+    for (int q = 0; q < MAXK; ++q) {
+      const int k = threadIdx.x + q * THREADS;
+      if (k <= n / 2) {
+        const int nk = (n - k) & (n - 1);
+        cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, k) : c_one<T>();
+        cplx<T> uk, unk, vk, vnk;
+        rfft_post(bu[k], bu[nk], tw, uk, unk);
+        rfft_post(bv[k], bv[nk], tw, vk, vnk);
+        cplx<T> pk = c_mul(uk, vk), pnk = c_mul(unk, vnk);
+        acc_k[q] = c_add(acc_k[q], mk(s_mul(pk.re, sg), s_mul(pk.im, sg)));
+        acc_nk[q] = c_add(acc_nk[q], mk(s_mul(pnk.re, sg), s_mul(pnk.im, sg)));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < MAXK; ++q) {
+    const int k = threadIdx.x + q * THREADS;
+    if (k <= n / 2) {
+      const int nk = (n - k) & (n - 1);
+      cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, k) : c_one<T>();
+      cplx<T> zk, znk;
+      irfft_pre(acc_k[q], acc_nk[q], tw, zk, znk);
+      bu[k] = zk;
+      if (k != 0 && nk != k) bu[nk] = znk;
+    }
+  }
+  __syncthreads();
+  cta_fft<T, THREADS, MAXE, true>(bu, g.lg_n, 1, g.tw, g.lg_P);
+  // acc holds 4 sigma U V; irfft_pre doubles it; inverse FFT scales by n
+  const float scale = 1.0f / (8.0f * (float)n);
+  for (int64_t t = threadIdx.x; t < g.N; t += THREADS) {
+    const cplx<T> z = bu[t >> 1];
+    T p = (t & 1) ? z.im : z.re;
+    st(out, t, div_count<T>(mul_scalar<T>(p, scale), cnt_recip_f(g, t)));
+  }
+}
+
+// ------------------------------------------------ four-step kernels
+// View the packed input z_t (t < n) as n1 x n2 row-major, t = n2 a + b.
+// A: column FFTs over a, twiddle W_n^{b c}, store Y[c][b].
+template <class T, int THREADS, int MAXE, int G, class In>
+__global__ void __launch_bounds__(THREADS) k_fs_col_fwd(Geom g, const In* __restrict__ x, int64_t ldx, int64_t glen,
+                                                        cplx<T>* __restrict__ Y, int lg_cb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int n1 = 1 << g.lg_n1, cb = 1 << lg_cb;
+  const int b0 = blockIdx.x << lg_cb;
+  const int64_t n = (int64_t)1 << g.lg_n;
+  x += (int64_t)blockIdx.y * ldx;
+  Y += (int64_t)blockIdx.y * n;
+  const int E = cb << g.lg_n1;
+  for (int e = threadIdx.x; e < E; e += THREADS) {
+    const int bb = e & (cb - 1), a = e >> lg_cb;
+    const int64_t t = ((int64_t)a << g.lg_n2) + b0 + bb;
+    buf[(bb << g.lg_n1) + a] = mk(gather<T, G>(g, x, glen, 2 * t), gather<T, G>(g, x, glen, 2 * t + 1));
+  }
+  __syncthreads();
+  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n1, cb, g.tw, g.lg_P);
+  for (int e = threadIdx.x; e < E; e += THREADS) {
+    const int bb = e & (cb - 1), c = e >> lg_cb;
+    const int64_t b = b0 + bb;
+    cplx<T> v = buf[(bb << g.lg_n1) + c];
+    const int64_t m = (2 * ((b * c) & (n - 1)));
+    if (m) v = c_mul(v, twiddle_M<T>(g.tA, g.tB, g.tws, m));
+    Y[((int64_t)c << g.lg_n2) + b] = v;
+  }
+  (void)n1;
+}
+
+// B: row pass over rows c and n1-c (block 0: rows 0 and n1/2).
+template <class T, int THREADS, int MAXE, int MODE>
+__global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict__ Y, RowArgs ra) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int n1 = 1 << g.lg_n1, n2 = 1 << g.lg_n2;
+  const int64_t n = (int64_t)1 << g.lg_n;
+  const int r0 = blockIdx.x == 0 ? 0 : blockIdx.x;
+  const int r1 = blockIdx.x == 0 ? n1 / 2 : n1 - blockIdx.x;
+  Y += (int64_t)blockIdx.y * n;
+  if (MODE != ROW_INV_LOAD) {
+    for (int e = threadIdx.x; e < 2 * n2; e += THREADS) {
+      const int row = e < n2 ? r0 : r1;
+      buf[e] = Y[((int64_t)row << g.lg_n2) + (e & (n2 - 1))];
+    }
+    __syncthreads();
+    cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n2, 2, g.tw, g.lg_P);
+  }
+  const int npairs = blockIdx.x == 0 ? n2 + 1 : n2;
+  const cplx<df64>* sin_ = ra.spec_in ? ra.spec_in + (int64_t)blockIdx.y * ra.ld_spec : nullptr;
+  cplx<df64>* sout = ra.spec_out ? ra.spec_out + (int64_t)blockIdx.y * ra.ld_spec : nullptr;
+  for (int p = threadIdx.x; p < npairs; p += THREADS) {
+    int sa, sb, ca, ea, cbr, eb;  // smem slots and (row, column) of the pair members
+    if (blockIdx.x == 0) {
+      if (p <= n2 / 2) {
+        ca = 0; ea = p; cbr = 0; eb = (n2 - p) & (n2 - 1);
+        sa = ea; sb = eb;
+      } else {
+        const int q = p - (n2 / 2 + 1);
+        ca = n1 / 2; ea = q; cbr = n1 / 2; eb = n2 - 1 - q;
+        sa = n2 + ea; sb = n2 + eb;
+      }
+    } else {
+      ca = r0; ea = p; cbr = r1; eb = n2 - 1 - p;
+      sa = ea; sb = n2 + eb;
+    }
+    const int64_t k = (int64_t)ca + ((int64_t)ea << g.lg_n1);   // natural index of member a
+    const bool k0 = (k == 0);
+    // perm-layout positions (row-major c * n2 + e); the partner of k = 0 is index n
+    const int64_t pa = ((int64_t)ca << g.lg_n2) + ea;
+    const int64_t pb = k0 ? n : ((int64_t)cbr << g.lg_n2) + eb;
+    cplx<T> tw = k0 ? c_one<T>() : twiddle_M<T>(g.tA, g.tB, g.tws, k);
+    cplx<T> pk, pnk;
+    if (MODE == ROW_INV_LOAD) {
+      const cplx<df64> a = sin_[pa], b = sin_[pb];
+      pk = mk(scal<T>::from_df(a.re), scal<T>::from_df(a.im));
+      pnk = mk(scal<T>::from_df(b.re), scal<T>::from_df(b.im));
+    } else {
+      cplx<T> wk, wnk;
+      rfft_post(buf[sa], buf[sb], tw, wk, wnk);
+      if (MODE == ROW_MATVEC) {
+        pk = mul_spec(wk, ra.chat[pa]);
+        pnk = mul_spec(wnk, ra.chat[pb]);
+      } else if (MODE == ROW_FWD_STORE) {
+        const float s = 0.5f * ra.scale;
+        wk = c_scale(wk, s);
+        wnk = c_scale(wnk, s);
+        const int64_t oa = ra.natural ? k : pa;
+        const int64_t ob = ra.natural ? (k0 ? n : n - k) : pb;
+        sout[oa] = mk(scal<T>::to_df(wk.re), scal<T>::to_df(wk.im));
+        if (!(k != 0 && sa == sb)) sout[ob] = mk(scal<T>::to_df(wnk.re), scal<T>::to_df(wnk.im));
+        continue;
+      } else {  // ROW_FWD_MUL_ACC: spec_out += weight * spec_in * W
+        const T sg = scal<T>::from_double(ra.weight[ra.weight_idx] * 0.5);
+        cplx<T> ua = mk(scal<T>::from_df(sin_[pa].re), scal<T>::from_df(sin_[pa].im));
+        cplx<T> ub = mk(scal<T>::from_df(sin_[pb].re), scal<T>::from_df(sin_[pb].im));
+        cplx<T> qa = c_mul(ua, wk), qb = c_mul(ub, wnk);
+        qa = mk(s_mul(qa.re, sg), s_mul(qa.im, sg));
+        qb = mk(s_mul(qb.re, sg), s_mul(qb.im, sg));
+        cplx<df64> oa = sout[pa];
+        sout[pa] = mk(df_add(oa.re, scal<T>::to_df(qa.re)), df_add(oa.im, scal<T>::to_df(qa.im)));
+        if (!(k != 0 && sa == sb)) {
+          cplx<df64> ob = sout[pb];
+          sout[pb] = mk(df_add(ob.re, scal<T>::to_df(qb.re)), df_add(ob.im, scal<T>::to_df(qb.im)));
+        }
+        continue;
+      }
+    }
+    cplx<T> zk, znk;
+    irfft_pre(pk, pnk, tw, zk, znk);
+    buf[sa] = zk;
+    if (!k0 && sb != sa) buf[sb] = znk;
+  }
+  if (MODE == ROW_FWD_STORE || MODE == ROW_FWD_MUL_ACC) return;
+  __syncthreads();
+  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n2, 2, g.tw, g.lg_P);
+  for (int e = threadIdx.x; e < 2 * n2; e += THREADS) {
+    const int row = e < n2 ? r0 : r1;
+    const int64_t b = e & (n2 - 1);
+    cplx<T> v = buf[e];
+    const int64_t m = 2 * ((b * row) & (n - 1));
+    if (m) v = c_mul_conj(v, twiddle_M<T>(g.tA, g.tB, g.tws, m));
+    Y[((int64_t)row << g.lg_n2) + b] = v;
+  }
+}
+
+// C: inverse column FFTs over c, unpack the real output and write the slice
+// (matvec) or the count-divided series (Hankelization).
+template <class T, int THREADS, int MAXE, int OUTM, class Out>
+__global__ void __launch_bounds__(THREADS) k_fs_col_inv(Geom g, const cplx<T>* __restrict__ Y, Out* __restrict__ y,
+                                                        int64_t ldy, int64_t out_off, int64_t out_cnt, float scale,
+                                                        int lg_cb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int cb = 1 << lg_cb;
+  const int b0 = blockIdx.x << lg_cb;
+  const int64_t n = (int64_t)1 << g.lg_n;
+  Y += (int64_t)blockIdx.y * n;
+  y += (int64_t)blockIdx.y * ldy;
+  const int E = cb << g.lg_n1;
+  for (int e = threadIdx.x; e < E; e += THREADS) {
+    const int bb = e & (cb - 1), c = e >> lg_cb;
+    buf[(bb << g.lg_n1) + c] = Y[((int64_t)c << g.lg_n2) + b0 + bb];
+  }
+  __syncthreads();
+  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n1, cb, g.tw, g.lg_P);
+  for (int e = threadIdx.x; e < 2 * E; e += THREADS) {
+    const int half = e & 1;
+    const int ee = e >> 1;
+    const int bb = ee & (cb - 1), a = ee >> lg_cb;
+    const int64_t t = ((int64_t)a << g.lg_n2) + b0 + bb;
+    const int64_t i = 2 * t + half;
+    const cplx<T> z = buf[(bb << g.lg_n1) + a];
+    T v = half ? z.im : z.re;
+    if (OUTM == OUT_SLICE) {
+      if (i >= out_off && i < out_off + out_cnt) st(y, i - out_off, mul_scalar<T>(v, scale));
+    } else {
+      if (i < g.N) st(y, i, div_count<T>(mul_scalar<T>(v, scale), cnt_recip_f(g, i)));
+    }
+  }
+}
+
+// ------------------------------------------------ host launchers
+static int lg2(int64_t x) {
+  int r = 0;
+  while (((int64_t)1 << r) < x) ++r;
+  return r;
+}
+
+template <class T> struct Lim;
+template <> struct Lim<float> { static constexpr int MAXE = 16384; };
+template <> struct Lim<df64> { static constexpr int MAXE = 8192; };
+constexpr int TH = 512;
+constexpr int TH_ROW = 256;
+constexpr int MAXE_ROW = 4096;
+
+// Opt each kernel into the dynamic shared memory it needs, once per size.
+template <class K> static void set_smem(K kern, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  if (bytes <= 48 * 1024) return;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = done[reinterpret_cast<const void*>(kern)];
+  if (bytes > cur) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cur = bytes;
+  }
+}
+
+bool small_path(const Geom& g, int prec) {
+  const int lim = prec == PREC_F32C ? Lim<float>::MAXE : Lim<df64>::MAXE;
+  return ((int64_t)1 << g.lg_n) <= lim;
+}
+
+int col_lg_cb(const Geom& g, int maxe) {
+  int lg = lg2(maxe) - g.lg_n1;
+  if (lg > g.lg_n2) lg = g.lg_n2;
+  if (lg < 0) lg = 0;
+  return lg;
+}
+
+template <class T, int G, class In>
+static void fs_forward(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s) {
+  constexpr int MAXE = Lim<T>::MAXE;
+  const int lg_cb = col_lg_cb(g, MAXE);
+  const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
+  auto kern = k_fs_col_fwd<T, TH, MAXE, G, In>;
+  set_smem(kern, sm);
+  dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
+  kern<<<grid, TH, sm, s>>>(g, x, ldx, glen, Y, lg_cb);
+}
+
+template <class T, int MODE>
+static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cudaStream_t s) {
+  const size_t sm = (size_t)(2 << g.lg_n2) * sizeof(cplx<T>);
+  auto kern = k_fs_row<T, TH_ROW, MAXE_ROW, MODE>;
+  set_smem(kern, sm);
+  dim3 grid((1 << g.lg_n1) / 2, batch);
+  kern<<<grid, TH_ROW, sm, s>>>(g, Y, ra);
+}
+
+template <class T, int OUTM, class Out>
+static void fs_inverse(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int64_t off, int64_t cnt, float scale,
+                       int batch, cudaStream_t s) {
+  constexpr int MAXE = Lim<T>::MAXE;
+  const int lg_cb = col_lg_cb(g, MAXE);
+  const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
+  auto kern = k_fs_col_inv<T, TH, MAXE, OUTM, Out>;
+  set_smem(kern, sm);
+  dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
+  kern<<<grid, TH, sm, s>>>(g, Y, y, ldy, off, cnt, scale, lg_cb);
+}
+
+// ---- public launchers (spectral.h)
+
+template <class T, class In, class Out>
+static void matvec_impl(const Geom& g, int transpose, const In* x, int64_t ldx, Out* y, int64_t ldy, int batch,
+                        const cplx<df64>* chat, void* scratch, bool small, cudaStream_t s) {
+  const int64_t off = transpose ? g.M - g.K : 0;
+  const int64_t cnt = transpose ? g.K : g.L;
+  if (small) {
+    constexpr int MAXE = Lim<T>::MAXE;
+    const size_t sm = (size_t)(1 << g.lg_n) * sizeof(cplx<T>);
+    if (transpose) {
+      auto kern = k_matvec_small<T, TH, MAXE, GATHER_XT, In, Out>;
+      set_smem(kern, sm);
+      kern<<<batch, TH, sm, s>>>(g, x, ldx, y, ldy, chat, off, cnt);
+    } else {
+      auto kern = k_matvec_small<T, TH, MAXE, GATHER_X, In, Out>;
+      set_smem(kern, sm);
+      kern<<<batch, TH, sm, s>>>(g, x, ldx, y, ldy, chat, off, cnt);
+    }
+    return;
+  }
+  cplx<T>* Y = reinterpret_cast<cplx<T>*>(scratch);
+  if (transpose) fs_forward<T, GATHER_XT, In>(g, x, ldx, 0, Y, batch, s);
+  else fs_forward<T, GATHER_X, In>(g, x, ldx, 0, Y, batch, s);
+  RowArgs ra{};
+  ra.chat = chat;
+  fs_row<T, ROW_MATVEC>(g, Y, ra, batch, s);
+  fs_inverse<T, OUT_SLICE, Out>(g, Y, y, ldy, off, cnt, 1.0f, batch, s);
+}
+
+void launch_matvec_df(const Geom& g, int prec, int transpose, const df64* x, int64_t ldx, df64* y, int64_t ldy,
+                      int batch, const cplx<df64>* chat, void* scratch, cudaStream_t s) {
+  const bool sm = small_path(g, prec);
+  if (prec == PREC_F32C) matvec_impl<float, df64, df64>(g, transpose, x, ldx, y, ldy, batch, chat, scratch, sm, s);
+  else matvec_impl<df64, df64, df64>(g, transpose, x, ldx, y, ldy, batch, chat, scratch, sm, s);
+}
+
+void launch_matvec_d(const Geom& g, int prec, int transpose, const double* x, int64_t ldx, double* y, int64_t ldy,
+                     int batch, const cplx<df64>* chat, void* scratch, cudaStream_t s) {
+  const bool sm = small_path(g, prec);
+  if (prec == PREC_F32C) matvec_impl<float, double, double>(g, transpose, x, ldx, y, ldy, batch, chat, scratch, sm, s);
+  else matvec_impl<df64, double, double>(g, transpose, x, ldx, y, ldy, batch, chat, scratch, sm, s);
+}
+
+// Spectrum of the circulant column, always in df64.  natural: 1 -> index k,
+// 0 -> four-step row-major order (c * n2 + e) with W_n at index n.
+void launch_spectrum(const Geom& g, const double* f, cplx<df64>* chat, int natural, float scale, void* scratch,
+                     cudaStream_t s) {
+  if (((int64_t)1 << g.lg_n) <= Lim<df64>::MAXE) {
+    const size_t sm = (size_t)(1 << g.lg_n) * sizeof(cplx<df64>);
+    auto kern = k_rfft_small<df64, TH, Lim<df64>::MAXE, GATHER_CIRC, double>;
+    set_smem(kern, sm);
+    kern<<<1, TH, sm, s>>>(g, f, 0, 0, chat, 0, scale);
+    return;
+  }
+  cplx<df64>* Y = reinterpret_cast<cplx<df64>*>(scratch);
+  fs_forward<df64, GATHER_CIRC, double>(g, f, 0, 0, Y, 1, s);
+  RowArgs ra{};
+  ra.spec_out = chat;
+  ra.natural = natural;
+  ra.scale = scale;
+  fs_row<df64, ROW_FWD_STORE>(g, Y, ra, 1, s);
+}
+
+template <class T, class Out>
+static void hankel_impl(const Geom& g, const df64* U, int64_t ldu, const df64* V, int64_t ldv, const double* sigma,
+                        const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
+                        const int* grp_idx_host, int m, Out* out, int64_t ldo, void* scratch, bool small,
+                        cudaStream_t s) {
+  if (small) {
+    constexpr int MAXE = Lim<T>::MAXE;
+    const size_t sm = (size_t)(2 << g.lg_n) * sizeof(cplx<T>);
+    auto kern = k_hankel_small<T, TH, MAXE, Out>;
+    set_smem(kern, sm);
+    kern<<<m, TH, sm, s>>>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, out, ldo);
+    return;
+  }
+  // large M: per component, forward FFT of u' (stored), forward FFT of v'
+  // multiplied into the group's accumulator; then one inverse per group.
+  const int64_t n = (int64_t)1 << g.lg_n;
+  cplx<T>* Y = reinterpret_cast<cplx<T>*>(scratch);
+  cplx<df64>* su = reinterpret_cast<cplx<df64>*>(reinterpret_cast<char*>(scratch) + n * sizeof(cplx<df64>));
+  cplx<df64>* acc = su + (n + 1);
+  for (int grp = 0; grp < m; ++grp) {
+    cudaMemsetAsync(acc, 0, (n + 1) * sizeof(cplx<df64>), s);
+    for (int ii = grp_off_host[grp]; ii < grp_off_host[grp + 1]; ++ii) {
+      const int comp = grp_idx_host[ii];
+      fs_forward<T, GATHER_PAD, df64>(g, U + (int64_t)comp * ldu, 0, g.L, Y, 1, s);
+      RowArgs ra{};
+      ra.spec_out = su;
+      ra.natural = 0;
+      ra.scale = 1.0f;
+      fs_row<T, ROW_FWD_STORE>(g, Y, ra, 1, s);
+      fs_forward<T, GATHER_PAD, df64>(g, V + (int64_t)comp * ldv, 0, g.K, Y, 1, s);
+      RowArgs rb{};
+      rb.spec_in = su;
+      rb.spec_out = acc;
+      rb.weight = sigma;
+      rb.weight_idx = comp;
+      fs_row<T, ROW_FWD_MUL_ACC>(g, Y, rb, 1, s);
+    }
+    RowArgs rc{};
+    rc.spec_in = acc;
+    fs_row<T, ROW_INV_LOAD>(g, Y, rc, 1, s);
+    fs_inverse<T, OUT_HANKEL, Out>(g, Y, out + (int64_t)grp * ldo, 0, 0, 0, 1.0f / (2.0f * (float)n), 1, s);
+  }
+}
+
+void launch_hankel(const Geom& g, int prec, const df64* U, int64_t ldu, const df64* V, int64_t ldv,
+                   const double* sigma, const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
+                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, cudaStream_t s) {
+  // the small kernel holds two length-n buffers
+  if (prec == PREC_F32C) {
+    const bool sm = ((int64_t)2 << g.lg_n) <= Lim<float>::MAXE;
+    hankel_impl<float, double>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, grp_off_host, grp_idx_host, m,
+                               out, ldo, scratch, sm, s);
+  } else {
+    const bool sm = ((int64_t)2 << g.lg_n) <= Lim<df64>::MAXE;
+    hankel_impl<df64, double>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, grp_off_host, grp_idx_host, m, out,
+                              ldo, scratch, sm, s);
+  }
+}
+
+size_t spectral_scratch_bytes(const Geom& g) {
+  const int64_t n = (int64_t)1 << g.lg_n;
+  // Y (n complex df64) + u spectrum and accumulator (n+1 complex df64 each)
+  return (size_t)(n + 2 * (n + 1)) * sizeof(cplx<df64>);
+}
+
+}  // namespace ssa

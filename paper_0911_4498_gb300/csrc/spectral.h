@@ -1,0 +1,49 @@
+// Host-side interface of the spectral kernels (spectral.cu).
+#pragma once
+#include "common.cuh"
+
+namespace ssa {
+
+enum { PREC_F64 = 0, PREC_F32C = 1 };
+enum { GATHER_X = 0, GATHER_XT = 1, GATHER_CIRC = 2, GATHER_PAD = 3 };
+enum { ROW_MATVEC = 0, ROW_FWD_STORE = 1, ROW_FWD_MUL_ACC = 2, ROW_INV_LOAD = 3 };
+enum { OUT_SLICE = 0, OUT_HANKEL = 1 };
+
+// FFT geometry of one (N, L) plan.  M = 2^(lg_n+1) >= N.  Small plans (one
+// CTA per transform) use tw = W_n^m; four-step plans split n = n1 * n2 with
+// n1 = 2^lg_n1 <= n2 = 2^lg_n2 and use tw = W_{n2}^m.  tA/tB give
+// W_M^m = tA[m >> tws] * tB[m & (2^tws - 1)].
+struct Geom {
+  int64_t N, L, K, M;
+  int lg_n, lg_n1, lg_n2;
+  const cplx<df64>* tw;
+  int lg_P;
+  const cplx<df64>* tA;
+  const cplx<df64>* tB;
+  int tws;
+};
+
+struct RowArgs {
+  const cplx<df64>* chat;      // ROW_MATVEC: scaled spectrum, four-step order
+  const cplx<df64>* spec_in;   // ROW_FWD_MUL_ACC / ROW_INV_LOAD input spectrum
+  cplx<df64>* spec_out;        // ROW_FWD_STORE / ROW_FWD_MUL_ACC output spectrum
+  int64_t ld_spec;             // batch stride of spec_in / spec_out
+  int natural;                 // ROW_FWD_STORE: natural index order (else four-step)
+  float scale;                 // ROW_FWD_STORE: multiply W by this power of two
+  const double* weight;        // ROW_FWD_MUL_ACC: sigma array on the device
+  int weight_idx;
+};
+
+bool small_path(const Geom& g, int prec);
+size_t spectral_scratch_bytes(const Geom& g);
+void launch_matvec_df(const Geom& g, int prec, int transpose, const df64* x, int64_t ldx, df64* y, int64_t ldy,
+                      int batch, const cplx<df64>* chat, void* scratch, cudaStream_t s);
+void launch_matvec_d(const Geom& g, int prec, int transpose, const double* x, int64_t ldx, double* y, int64_t ldy,
+                     int batch, const cplx<df64>* chat, void* scratch, cudaStream_t s);
+void launch_spectrum(const Geom& g, const double* f, cplx<df64>* chat, int natural, float scale, void* scratch,
+                     cudaStream_t s);
+void launch_hankel(const Geom& g, int prec, const df64* U, int64_t ldu, const df64* V, int64_t ldv,
+                   const double* sigma, const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
+                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, cudaStream_t s);
+
+}  // namespace ssa

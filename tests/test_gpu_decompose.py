@@ -1,0 +1,126 @@
+"""GPU parity of the whole decomposition (GKL with CGS2, thick restart, projected
+SVD, Ritz vectors, sign rule) and of ssa_reconstruct, against the oracle and
+closed forms."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_0911_4498_gb300 as ssa
+from oracle import ssa as ossa
+from oracle import trajectory
+from paper_0911_4498_gb300 import synth
+from ssa_testlib import compare_vectors, gpu_decompose, gpu_decompose_reconstruct
+
+pytestmark = pytest.mark.gpu
+
+SIG_F64 = 1e-10     # sigma relative error, FP64-class path
+REC_F64 = 1e-9      # reconstruction relative L2 error
+SIG_F32C = 1e-5
+
+
+def _rel(a, b):
+    return np.abs(a - b) / np.abs(b)
+
+
+def test_three_sines_N1000_full_pipeline():
+    N, L, k = 1000, 500, 10
+    f = synth.three_sines(N, seed=0)
+    ref = ossa.decompose(f, L, k, method="jacobi")
+    groups = [[i] for i in range(k)]
+    got = gpu_decompose_reconstruct(f, L, k, groups)
+    assert got["rc"] == ssa.SSA_OK and got["info"]["converged"]
+    assert np.max(_rel(got["sigma"], ref["sigma"])) <= SIG_F64
+    compare_vectors(got["U"], ref["U"], ref["sigma"], 1e-8)
+    compare_vectors(got["V"], ref["V"], ref["sigma"], 1e-8)
+    rec_ref = ossa.reconstruct(N, L, ref["sigma"], ref["U"], ref["V"], groups)
+    for g in range(k):
+        err = np.linalg.norm(got["rec"][g] - rec_ref[g]) / np.linalg.norm(rec_ref[g])
+        assert err <= REC_F64, (g, err)
+    # the GPU's own triples Hankelize (through the oracle) to the same series
+    rec_own = ossa.reconstruct(N, L, got["sigma"], got["U"], got["V"], groups)
+    assert np.max(np.abs(rec_own - got["rec"])) <= 1e-11 * np.abs(f).max()
+    # sign rule
+    for i in range(k):
+        u = got["U"][:, i]
+        assert u[np.argmax(np.abs(u))] > 0
+
+
+@pytest.mark.parametrize("N,L,k", [(37, 12, 3), (129, 64, 5), (257, 100, 8), (500, 250, 8), (777, 300, 12),
+                                   (2049, 1024, 6), (5000, 1667, 10)])
+def test_ragged_sizes_match_oracle(N, L, k):
+    f = synth.three_sines(N, seed=N)
+    ref = ossa.decompose(f, L, k, method="jacobi" if N <= 1500 else "lanczos")
+    got = gpu_decompose(f, L, k)
+    assert got["rc"] == ssa.SSA_OK
+    assert np.max(np.abs(got["sigma"] - ref["sigma"]) / ref["sigma"]) <= SIG_F64
+    compare_vectors(got["U"], ref["U"], ref["sigma"], 1e-7)
+
+
+def test_window_larger_than_K():
+    f = synth.three_sines(600, seed=8)
+    ref = ossa.decompose(f, 450, 6, method="jacobi")
+    got = gpu_decompose(f, 450, 6)
+    assert got["U"].shape == (450, 6) and got["V"].shape == (151, 6)
+    assert np.max(_rel(got["sigma"], ref["sigma"])) <= SIG_F64
+    compare_vectors(got["U"], ref["U"], ref["sigma"], 1e-8)
+    compare_vectors(got["V"], ref["V"], ref["sigma"], 1e-8)
+
+
+def test_geometric_series_rank_one_breakdown():
+    N, L, a = 300, 120, 0.99
+    K = N - L + 1
+    f = synth.geometric(N, a)
+    x = a ** np.arange(L)
+    y = a ** np.arange(K)
+    s1 = a * np.linalg.norm(x) * np.linalg.norm(y)
+    got = gpu_decompose(f, L, 4)
+    assert got["rc"] == ssa.SSA_OK
+    assert abs(got["sigma"][0] - s1) <= 1e-12 * s1
+    assert np.all(np.abs(got["sigma"][1:]) <= 1e-12 * s1)
+    assert abs(abs(got["U"][:, 0] @ x) / np.linalg.norm(x) - 1) <= 1e-12
+
+
+def test_periodic_cosine_rank_two():
+    T, L, K, A = 10, 50, 60, 3.0
+    N = L + K - 1
+    f = synth.cosine(N, T, A, 0.7)
+    got = gpu_decompose(f, L, 3)
+    want = A * math.sqrt(L * K) / 2
+    np.testing.assert_allclose(got["sigma"][:2], [want, want], rtol=1e-12)
+    assert got["sigma"][2] <= 1e-12 * want
+
+
+def test_zero_series():
+    got = gpu_decompose(np.zeros(64), 20, 3)
+    assert np.all(got["sigma"] == 0.0)
+
+
+def test_full_rank_request_and_frobenius():
+    N, L = 60, 20
+    f = synth.three_sines(N, seed=4)
+    got = gpu_decompose(f, L, L)
+    frob = np.sum(trajectory.antidiagonal_counts(N, L) * f * f)
+    assert abs(np.sum(got["sigma"] ** 2) - frob) <= 1e-11 * frob
+
+
+def test_two_seeds_agree():
+    f = synth.three_sines(1000, seed=0)
+    a = gpu_decompose(f, 500, 10, seed=1)
+    b = gpu_decompose(f, 500, 10, seed=2)
+    assert np.max(_rel(a["sigma"], b["sigma"])) <= SIG_F64
+
+
+def test_f32c_precision_mode():
+    N, L, k = 1000, 500, 10
+    f = synth.three_sines(N, seed=0)
+    ref = ossa.decompose(f, L, k, method="jacobi")
+    got = gpu_decompose(f, L, k, precision=ssa.SSA_PREC_F32C)
+    assert np.max(_rel(got["sigma"], ref["sigma"])) <= SIG_F32C
+
+
+def test_bad_k_rejected():
+    with pytest.raises(ssa.SSAError):
+        gpu_decompose(synth.three_sines(100, 1), 40, 41)
+    with pytest.raises(ssa.SSAError):
+        gpu_decompose(synth.three_sines(100, 1), 40, 0)
