@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput of the fast Basic SSA hot path on one or more GB300s.
+
+One step = one whole pass of the hot path on the long-series workload:
+spectrum of the series (Algorithm 2 steps 1-2), thick-restart Lanczos SVD of
+the N = 2^20, L = 2^19 trajectory matrix for k = 50 triples (Algorithms 1-3),
+and Hankelization of all k elementary components (Algorithm 4).  The metric
+is decompositions per second (each including its reconstruction).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f64|f32c]
+  python bench.py --impl reference ...   # the CPU oracle on this host's cores
+
+Multi-GPU (torchrun, one rank per GPU) runs independent replicas: the path
+does not shard within one series, so each rank decomposes its
+own series and value = all ranks' decompositions / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SSA decomps/sec & matvec HBM GB/s vs peak at stated sigma error; p50/p99 latency"
+UNIT = "decomps/s"
+
+WORKLOADS = {
+    # long series: 20 sinusoids (periods log-uniform in [5, 5000], amplitudes 1/i) + trend + N(0, 0.1^2)
+    "many_sines_N1M": dict(N=1 << 20, L=1 << 19, k=50, gen="many_sines", seed=1,
+                           golden="tests/golden/sigma_many_sines_N1048576_L524288_k50.txt"),
+    # half-length variant, used for profiling captures (bases ~0.9 GB, still larger than L2)
+    "many_sines_N512K": dict(N=1 << 19, L=1 << 18, k=50, gen="many_sines", seed=1, golden=None),
+    # N = 1000 three-sine series (the paper-sized small case)
+    "three_sines_N1000": dict(N=1000, L=500, k=10, gen="three_sines", seed=0, golden=None),
+}
+
+# ncu DRAM traffic per launch of the dominant kernel, keyed by kernel name;
+# valid only while the kernel source is unchanged (sha256 of its file).
+NCU_TRAFFIC = {}
+
+
+def series(w):
+    from paper_0911_4498_gb300 import synth
+    return getattr(synth, w["gen"])(w["N"], seed=w["seed"])
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def read_golden(path):
+    if not path or not os.path.exists(os.path.join(ROOT, path)):
+        return None
+    out = {}
+    with open(os.path.join(ROOT, path)) as fh:
+        for line in fh:
+            if line.startswith("#") or ":" not in line:
+                continue
+            k, _, v = line.partition(":")
+            out[k.strip()] = np.array([float(t) for t in v.split()])
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.dev is not None:
+            cmd += ["-i", str(self.dev)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = list(csv.reader(io.StringIO(open(self.path).read())))
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index_for_smi(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return local_rank
+
+
+# ----------------------------------------------------------------- CPU oracle sample
+def cpu_worker(args):
+    """Run the oracle's Lanczos for a bounded number of half-steps (own process, 1 thread)."""
+    from oracle import ssa as ossa
+    w = WORKLOADS[args.workload]
+    f = series(w)
+    t = time.perf_counter()
+    out = ossa.decompose(f, w["L"], w["k"], method="lanczos", max_steps=args.sample_halfsteps)
+    dt = time.perf_counter() - t
+    print(json.dumps({"seconds": dt, "halfsteps": int(out.get("steps", args.sample_halfsteps))}))
+
+
+def cpu_sample(workload, halfsteps):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", workload,
+                        "--sample-halfsteps", str(halfsteps)], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("cpu worker failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(workload, halfsteps_full, sample_halfsteps):
+    s = cpu_sample(workload, sample_halfsteps)
+    # decomps/s extrapolated from the sampled half-steps to a whole decomposition
+    value = (s["halfsteps"] / max(halfsteps_full, 1)) / s["seconds"]
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"first {s['halfsteps']} Lanczos half-steps (matvec + MGS-twice reorthogonalisation) of "
+                       f"the same decomposition in {s['seconds']:.1f} s, scaled to the {halfsteps_full} half-steps "
+                       "a full decomposition takes (early half-steps have the smallest bases, so this favours "
+                       "the CPU); reconstruction not included")}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    full = args.ref_halfsteps_full
+    vals = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_sample(args.workload, args.sample_halfsteps)
+        if i >= args.warmup:
+            vals.append((s["halfsteps"] / full) / s["seconds"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": w["N"], "L": w["L"], "k": w["k"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: first {args.sample_halfsteps} Lanczos half-steps of the CPU "
+                                       f"oracle, scaled to {full} half-steps per decomposition"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_0911_4498_gb300 import build
+    build.build()
+    import paper_0911_4498_gb300 as ssa
+
+    w = WORKLOADS[args.workload]
+    N, L, k = w["N"], w["L"], w["k"]
+    K = N - L + 1
+    prec = ssa.SSA_PREC_F32C if args.precision == "f32c" else ssa.SSA_PREC_F64
+    stream = torch.cuda.current_stream()
+    opts = ssa.make_opts(precision=prec, seed=rank, stream=stream.cuda_stream)
+    f_host = series(w)
+    plan = ssa.ssa_embed_plan(N, L, opts)
+    f_dev = torch.from_numpy(f_host).cuda()
+    groups = [[i] for i in range(k)]
+    off, idx = ssa.groups_csr(groups)
+    off_dev = torch.from_numpy(off).cuda()
+    idx_dev = torch.from_numpy(idx).cuda()
+    out_dev = torch.empty((k, N), dtype=torch.float64, device="cuda")
+    sig_dev = torch.empty(k, dtype=torch.float64, device="cuda")
+    info = {}
+
+    def step(fin, out, sig):
+        d, rc = ssa.ssa_decompose(plan, fin, k)
+        try:
+            ssa.ssa_reconstruct(d, off_dev, idx_dev, k, out)
+            ssa.ssa_decomp_get(d, sig, None, None, None)
+            info.update(ssa.ssa_decomp_info(d))
+            info["rc"] = rc
+        finally:
+            ssa.ssa_decomp_destroy(d)
+
+    for _ in range(args.warmup):
+        step(f_dev, out_dev, sig_dev)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(gpu_index_for_smi(local))
+    sampler.start()
+    ssa.ssa_stats_enable(True)
+    launches0 = ssa.ssa_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        step(f_dev, out_dev, sig_dev)
+        lat.append(time.perf_counter() - t)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = ssa.ssa_kernel_launches() - launches0
+    stats = ssa.ssa_stats_get()
+    ssa.ssa_stats_enable(False)
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    value = world * args.steps / (elapsed_ms / 1000.0)
+
+    # accuracy against the oracle's stored values
+    sig = sig_dev.cpu().numpy()
+    gold = read_golden(w.get("golden"))
+    sig_err = None
+    if gold is not None:
+        ref = gold["sigma"][:k]
+        sig_err = float(np.max(np.abs(sig - ref) / ref))
+
+    # roofline of the kernel with the most device time
+    hbm, peak_kind = peaks()
+    cand = [s for s in stats if s["name"] not in ("misc", "gated") and s["launches"] > 0]
+    dom = max(cand, key=lambda s: s["ms"]) if cand else None
+    roof = None
+    if dom:
+        achieved = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": NCU_TRAFFIC.get(dom["name"]), "kernel": dom["name"],
+                "bytes_per_launch": dom["bytes"] / dom["launches"], "ms_per_launch": dom["ms"] / dom["launches"],
+                "launches": dom["launches"], "peak_source": peak_kind}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        f_pin = torch.from_numpy(f_host).pin_memory()
+        out_pin = torch.empty((k, N), dtype=torch.float64).pin_memory()
+        sig_pin = torch.empty(k, dtype=torch.float64).pin_memory()
+        n_e2e = max(1, args.steps)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(n_e2e):
+            step(f_pin, out_pin, sig_pin)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        if dist:
+            tt = torch.tensor([dt], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": world * n_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+               "d2h_bytes_per_step": 8 * k + 8 * k * N}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, int(info.get("matvecs", 1)), args.sample_halfsteps)
+
+    ssa.ssa_plan_destroy(plan)
+    if rank == 0:
+        per_kernel = {s["name"]: {"launches": s["launches"], "ms": round(s["ms"], 3),
+                                  "GBps": round(s["bytes"] / (s["ms"] / 1e3) / 1e9, 1) if s["ms"] > 0 else None}
+                      for s in stats if s["launches"]}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "df64" if prec == ssa.SSA_PREC_F64 else "f32+df64", "data": "synthetic",
+                "config": {"workload": args.workload, "N": N, "L": L, "K": K, "k": k, "groups": "k elementary",
+                           "precision": args.precision, "parallelism": f"replicas x{world}",
+                           "l2": "working set (Lanczos bases, ~1.7 GB) is larger than L2; no flush"},
+                "sigma_rel_err_max": sig_err, "converged": bool(info.get("converged")),
+                "restarts": info.get("restarts"), "matvecs_per_decomp": info.get("matvecs"),
+                "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "kernels": per_kernel}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="many_sines_N1M", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32c"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample-halfsteps", type=int, default=6)
+    ap.add_argument("--ref-halfsteps-full", type=int, default=400)
+    ap.add_argument("--cpu-worker", action="store_true")
+    args = ap.parse_args()
+    if args.cpu_worker:
+        cpu_worker(args)
+        return 0
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -151,6 +151,31 @@ int ssa_reconstruct(ssa_decomp_t d, const int32_t* grp_off, const int32_t* grp_i
 int ssa_hankelize(ssa_plan_t plan, const double* sigma, const double* U, int64_t ldu, const double* V, int64_t ldv,
                   int r, const int32_t* grp_off, const int32_t* grp_idx, int m, double* out);
 
+/* ---- launch accounting (not part of the paper's method) ---------------- */
+
+/* One entry per kernel of the library: launches, summed device time from
+   CUDA events recorded around each launch, and the algorithmic bytes and
+   flops charged to those launches (what the method must move / compute,
+   e.g. one read of the basis for a projection). */
+typedef struct ssa_kernel_stat {
+  char name[32];
+  uint64_t launches;
+  double ms;
+  double bytes;
+  double flops;
+} ssa_kernel_stat_t;
+
+/* on = 1: reset the per-kernel statistics and start recording (a pair of
+   CUDA events around every launch, on the launch's stream); on = 0: stop. */
+int ssa_stats_enable(int on);
+
+/* Synchronise the device, then copy up to max entries to out; *count gets
+   the number of kernel entries available. */
+int ssa_stats_get(ssa_kernel_stat_t* out, int max, int* count);
+
+/* Total kernels launched by the library in this process. */
+uint64_t ssa_kernel_launches(void);
+
 void ssa_plan_destroy(ssa_plan_t plan);
 void ssa_decomp_destroy(ssa_decomp_t d);
 const char* ssa_strerror(int code);

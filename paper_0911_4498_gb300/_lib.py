@@ -26,6 +26,11 @@ class SsaOpts(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
 class SSAError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{msg} (status {code})")
@@ -49,6 +54,9 @@ _SIGS = {
     "ssa_hankelize": (_I, [_VP, _VP, _VP, _I64, _VP, _I64, _I, _VP, _VP, _I, _VP]),
     "ssa_plan_destroy": (None, [_VP]),
     "ssa_decomp_destroy": (None, [_VP]),
+    "ssa_stats_enable": (_I, [_I]),
+    "ssa_stats_get": (_I, [ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
+    "ssa_kernel_launches": (ctypes.c_uint64, []),
     "ssa_strerror": (ctypes.c_char_p, [_I]),
     "ssa_last_error": (ctypes.c_char_p, []),
 }
@@ -170,6 +178,23 @@ def ssa_plan_destroy(plan):
 
 def ssa_decomp_destroy(d):
     lib().ssa_decomp_destroy(d)
+
+
+def ssa_stats_enable(on: bool):
+    _check(lib().ssa_stats_enable(1 if on else 0))
+
+
+def ssa_stats_get():
+    """Per-kernel stats as a list of dicts (name, launches, ms, bytes, flops)."""
+    arr = (KernelStat * 64)()
+    n = _I()
+    _check(lib().ssa_stats_get(arr, 64, ctypes.byref(n)))
+    return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches), "ms": arr[i].ms,
+             "bytes": arr[i].bytes, "flops": arr[i].flops} for i in range(min(n.value, 64))]
+
+
+def ssa_kernel_launches() -> int:
+    return int(lib().ssa_kernel_launches())
 
 
 def ssa_strerror(code: int) -> str:

@@ -5,13 +5,16 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "ssa.h"
 #include "lanczos.h"
 #include "spectral.h"
+#include "prof.h"
 
 using namespace ssa;
 
@@ -231,6 +234,117 @@ struct ssa_decomp_s {
   df64* Uw = nullptr;       // Lw x k (working orientation, for Hankelization)
   df64* Vw = nullptr;       // Kw x k
 };
+
+
+// ------------------------------------------------------------------ launch stats
+namespace ssa {
+static const char* const kClassNames[K_NCLASS] = {
+    "spectrum", "matvec_small", "matvec_colfwd", "matvec_row", "matvec_colinv", "cgs_proj", "cgs_update",
+    "normalize", "small_svd", "ritz", "hankel_small", "hankel_fourstep", "misc", "gated"};
+struct PendingLaunch {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes, flops;
+  int launches;
+};
+struct ClassAcc {
+  uint64_t launches = 0;
+  double ms = 0, bytes = 0, flops = 0;
+};
+static std::mutex g_pmu;
+static bool g_pon = false;
+static std::atomic<uint64_t> g_launches{0};
+static std::vector<PendingLaunch> g_pending;
+static std::vector<cudaEvent_t> g_evpool;
+static ClassAcc g_acc[K_NCLASS];
+static thread_local cudaEvent_t g_begin = nullptr;
+
+static cudaEvent_t ev_get() {
+  if (!g_evpool.empty()) {
+    cudaEvent_t e = g_evpool.back();
+    g_evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+bool prof_enabled() { return g_pon; }
+void prof_begin(cudaStream_t s) {
+  if (!g_pon) return;
+  std::lock_guard<std::mutex> lk(g_pmu);
+  g_begin = ev_get();
+  cudaEventRecord(g_begin, s);
+}
+void prof_end(cudaStream_t s, int cls, double bytes, double flops, int launches) {
+  g_launches += launches;
+  if (!g_pon || !g_begin) return;
+  std::lock_guard<std::mutex> lk(g_pmu);
+  cudaEvent_t e = ev_get();
+  cudaEventRecord(e, s);
+  g_pending.push_back({cls, g_begin, e, bytes, flops, launches});
+  g_begin = nullptr;
+}
+void prof_flush() {
+  std::lock_guard<std::mutex> lk(g_pmu);
+  std::vector<PendingLaunch> keep;
+  for (auto& pl : g_pending) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, pl.a, pl.b);
+    if (e == cudaErrorNotReady) {
+      cudaGetLastError();
+      keep.push_back(pl);
+      continue;
+    }
+    if (e == cudaSuccess) {
+      ClassAcc& c = g_acc[pl.cls];
+      c.launches += pl.launches;
+      c.ms += ms;
+      c.bytes += pl.bytes;
+      c.flops += pl.flops;
+    } else {
+      cudaGetLastError();
+    }
+    g_evpool.push_back(pl.a);
+    g_evpool.push_back(pl.b);
+  }
+  g_pending.swap(keep);
+}
+}  // namespace ssa
+
+extern "C" int ssa_stats_enable(int on) {
+  {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    if (on) {
+      for (auto& c : g_acc) c = ClassAcc{};
+      for (auto& pl : g_pending) {
+        g_evpool.push_back(pl.a);
+        g_evpool.push_back(pl.b);
+      }
+      g_pending.clear();
+    }
+    g_pon = on != 0;
+  }
+  return SSA_OK;
+}
+
+extern "C" int ssa_stats_get(ssa_kernel_stat_t* out, int max, int* count) {
+  CK(cudaDeviceSynchronize());
+  prof_flush();
+  std::lock_guard<std::mutex> lk(g_pmu);
+  if (count) *count = K_NCLASS;
+  for (int i = 0; i < K_NCLASS && i < max && out; ++i) {
+    std::memset(&out[i], 0, sizeof out[i]);
+    std::snprintf(out[i].name, sizeof out[i].name, "%s", kClassNames[i]);
+    out[i].launches = g_acc[i].launches;
+    out[i].ms = g_acc[i].ms;
+    out[i].bytes = g_acc[i].bytes;
+    out[i].flops = g_acc[i].flops;
+  }
+  return SSA_OK;
+}
+
+extern "C" uint64_t ssa_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" void ssa_default_opts(ssa_opts_t* o) {
   if (!o) return;
@@ -574,6 +688,7 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     CK(cudaMemcpyAsync(&converged, w.sw.conv, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&status, w.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (prof_enabled()) prof_flush();
     if (status & SSA_DEV_NONFINITE) {
       set_err("non-finite value in the Lanczos recurrence");
       return SSA_ENUMERIC;

@@ -6,6 +6,7 @@
 // and the projected problem are double-float (df64).
 #include <cooperative_groups.h>
 #include "lanczos.h"
+#include "prof.h"
 
 namespace ssa {
 
@@ -501,34 +502,53 @@ int reorth_blocks(int64_t dim) { return (int)((dim + SLAB - 1) / SLAB); }
 void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, const int* flag,
                  cudaStream_t s) {
   const int G = reorth_blocks(dim);
+  // algorithmic bytes: the ncols basis columns once, w read (and written by the update)
+  const double qb = 8.0 * (double)dim * ncols;
+  const double fl = 2.0 * (double)dim * ncols;
   if (ncols > 0) {
+    prof_begin(s);
     k_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, rw.h, rw.counter, flag);
+    prof_end(s, flag ? K_GATED : K_PROJ, flag ? 0.0 : qb + 8.0 * dim, flag ? 0.0 : fl);
+    prof_begin(s);
     k_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
+    prof_end(s, flag ? K_GATED : K_UPDATE, flag ? 0.0 : qb + 16.0 * dim, flag ? 0.0 : fl);
+    prof_begin(s);
     k_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, rw.h, rw.counter, flag);
+    prof_end(s, flag ? K_GATED : K_PROJ, flag ? 0.0 : qb + 8.0 * dim, flag ? 0.0 : fl);
   }
+  prof_begin(s);
   k_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
+  prof_end(s, flag ? K_GATED : K_UPDATE, flag ? 0.0 : qb + 16.0 * dim, flag ? 0.0 : fl);
 }
 
 void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est, int* flag, int mode,
                       uint64_t seed, uint64_t stream, unsigned* status, cudaStream_t s) {
+  prof_begin(s);
   k_normalize<<<grid_for(dim, 256, 1184), 256, 0, s>>>(w, dim, rw.nrm, qcol, bentry, est, flag, mode, seed, stream,
                                                        status);
+  prof_end(s, mode == 0 ? K_NORMALIZE : K_GATED, mode == 0 ? 16.0 * dim : 0.0, 0.0);
 }
 
 void launch_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stream, cudaStream_t s) {
+  prof_begin(s);
   k_random_fill<<<grid_for(dim, 256, 1184), 256, 0, s>>>(w, dim, seed, stream);
+  prof_end(s, K_MISC, 8.0 * dim, 0.0);
 }
 
 void launch_small_svd(const df64* B, int ldb, int r, int c, const int2* sched, SvdWork& sw, int k, double tol_conv,
                       df64* est, unsigned* status, cudaStream_t s) {
   const int cc = c + (c & 1);
+  prof_begin(s);
   k_small_svd<<<1, SVD_THREADS, 0, s>>>(B, ldb, r, c, sw.A, sw.W, sched, cc, sw.sigma, sw.P, sw.Q, sw.resid,
                                          sw.sigma_d, k, tol_conv, sw.conv, est, status, sw.max_sweeps, sw.rot_tol);
+  prof_end(s, K_SMALL_SVD, 0.0, 0.0);
 }
 
 void launch_restart_B(df64* B, int ldb, int nrows_clear, const SvdWork& sw, int r, int kk, int c_old,
                       cudaStream_t s) {
+  prof_begin(s);
   k_restart_B<<<1, 512, 0, s>>>(B, ldb, nrows_clear, sw.sigma, sw.P, r, kk, df_zero(), c_old);
+  prof_end(s, K_MISC, 0.0, 0.0);
 }
 
 void launch_ritz(const df64* Q, int64_t ldq, int r, const df64* P, int ldp, int ncol, df64* out, int64_t ldo,
@@ -540,29 +560,41 @@ void launch_ritz(const df64* Q, int64_t ldq, int r, const df64* P, int ldp, int 
     cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(MAXCOL + 2) * 32 * 8);
     attr = true;
   }
+  prof_begin(s);
   k_ritz<<<grid, 256, sm, s>>>(Q, ldq, r, P, ldp, ncol, out, ldo, dim);
+  prof_end(s, K_RITZ, 8.0 * (double)dim * (r + ncol), 2.0 * (double)dim * r * ncol);
 }
 
 void launch_copy_df(const df64* src, df64* dst, int64_t n, cudaStream_t s) {
+  prof_begin(s);
   k_copy_df<<<grid_for(n, 256, 1184), 256, 0, s>>>(src, dst, n);
+  prof_end(s, K_MISC, 16.0 * n, 0.0);
 }
 
 void launch_sign(const df64* U, int64_t ldu, int64_t dim, int k, int* sgn, cudaStream_t s) {
+  prof_begin(s);
   k_sign<<<k, 1024, 0, s>>>(U, ldu, dim, sgn);
+  prof_end(s, K_MISC, 8.0 * (double)dim * k, 0.0);
 }
 
 void launch_store_cols(const df64* src, int64_t lds, int64_t dim, int ncol, const int* sgn, double* dst, int64_t ldd,
                        cudaStream_t s) {
+  prof_begin(s);
   k_store_cols<<<grid_for(dim * ncol, 256, 4736), 256, 0, s>>>(src, lds, dim, ncol, sgn, dst, ldd);
+  prof_end(s, K_MISC, 16.0 * (double)dim * ncol, 0.0);
 }
 
 void launch_df_to_double(const df64* src, double* dst, int64_t n, cudaStream_t s) {
+  prof_begin(s);
   k_df_to_double<<<grid_for(n, 256, 1184), 256, 0, s>>>(src, dst, n);
+  prof_end(s, K_MISC, 16.0 * n, 0.0);
 }
 
 void launch_double_to_df(const double* src, int64_t lds, df64* dst, int64_t ldd, int64_t dim, int ncol,
                          cudaStream_t s) {
+  prof_begin(s);
   k_double_to_df<<<grid_for(dim * ncol, 256, 4736), 256, 0, s>>>(src, lds, dst, ldd, dim, ncol);
+  prof_end(s, K_MISC, 16.0 * (double)dim * ncol, 0.0);
 }
 
 }  // namespace ssa

@@ -1,0 +1,33 @@
+// Per-kernel launch accounting: a launch counter and optional CUDA-event
+// timing around every kernel launch, with the algorithmic bytes and flops
+// each launch is charged (used for roofline reporting).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ssa {
+
+enum KClass {
+  K_SPECTRUM = 0,
+  K_MATVEC_SMALL,
+  K_MATVEC_COLFWD,
+  K_MATVEC_ROW,
+  K_MATVEC_COLINV,
+  K_PROJ,
+  K_UPDATE,
+  K_NORMALIZE,
+  K_SMALL_SVD,
+  K_RITZ,
+  K_HANKEL_SMALL,
+  K_HANKEL_FS,
+  K_MISC,
+  K_GATED,
+  K_NCLASS
+};
+
+void prof_begin(cudaStream_t s);
+void prof_end(cudaStream_t s, int cls, double bytes, double flops, int launches = 1);
+void prof_flush();
+bool prof_enabled();
+
+}  // namespace ssa

@@ -21,6 +21,7 @@
 #include <unordered_map>
 #include "spectral.h"
 #include "fft.cuh"
+#include "prof.h"
 
 namespace ssa {
 
@@ -403,35 +404,42 @@ int col_lg_cb(const Geom& g, int maxe) {
 }
 
 template <class T, int G, class In>
-static void fs_forward(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s) {
+static void fs_forward(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s,
+                       int cls, double bytes) {
   constexpr int MAXE = Lim<T>::MAXE;
   const int lg_cb = col_lg_cb(g, MAXE);
   const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
   auto kern = k_fs_col_fwd<T, TH, MAXE, G, In>;
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
+  prof_begin(s);
   kern<<<grid, TH, sm, s>>>(g, x, ldx, glen, Y, lg_cb);
+  prof_end(s, cls, bytes, 5.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n1 * batch, 1);
 }
 
 template <class T, int MODE>
-static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cudaStream_t s) {
+static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cudaStream_t s, int cls, double bytes) {
   const size_t sm = (size_t)(2 << g.lg_n2) * sizeof(cplx<T>);
   auto kern = k_fs_row<T, TH_ROW, MAXE_ROW, MODE>;
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n1) / 2, batch);
+  prof_begin(s);
   kern<<<grid, TH_ROW, sm, s>>>(g, Y, ra);
+  prof_end(s, cls, bytes, 10.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n2 * batch, 1);
 }
 
 template <class T, int OUTM, class Out>
 static void fs_inverse(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int64_t off, int64_t cnt, float scale,
-                       int batch, cudaStream_t s) {
+                       int batch, cudaStream_t s, int cls, double bytes) {
   constexpr int MAXE = Lim<T>::MAXE;
   const int lg_cb = col_lg_cb(g, MAXE);
   const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
   auto kern = k_fs_col_inv<T, TH, MAXE, OUTM, Out>;
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
+  prof_begin(s);
   kern<<<grid, TH, sm, s>>>(g, Y, y, ldy, off, cnt, scale, lg_cb);
+  prof_end(s, cls, bytes, 5.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n1 * batch, 1);
 }
 
 // ---- public launchers (spectral.h)
@@ -441,27 +449,39 @@ static void matvec_impl(const Geom& g, int transpose, const In* x, int64_t ldx, 
                         const cplx<df64>* chat, void* scratch, bool small, cudaStream_t s) {
   const int64_t off = transpose ? g.M - g.K : 0;
   const int64_t cnt = transpose ? g.K : g.L;
+  // algorithmic traffic of a product (section 8(d)): the input and output
+  // vectors and the half spectrum; flops of two real FFTs and the multiply
+  const double n = (double)((int64_t)1 << g.lg_n);
+  const double in_b = (double)sizeof(In) * (transpose ? g.L : g.K) * batch;
+  const double out_b = (double)sizeof(Out) * cnt * batch;
+  const double spec_b = 16.0 * (n + 1);
+  const double mv_bytes = in_b + out_b + spec_b;
+  const double mv_flops = (5.0 * (double)g.M * (g.lg_n + 1) + 3.0 * (double)g.M) * batch;
   if (small) {
     constexpr int MAXE = Lim<T>::MAXE;
     const size_t sm = (size_t)(1 << g.lg_n) * sizeof(cplx<T>);
     if (transpose) {
       auto kern = k_matvec_small<T, TH, MAXE, GATHER_XT, In, Out>;
       set_smem(kern, sm);
+      prof_begin(s);
       kern<<<batch, TH, sm, s>>>(g, x, ldx, y, ldy, chat, off, cnt);
+      prof_end(s, K_MATVEC_SMALL, mv_bytes, mv_flops);
     } else {
       auto kern = k_matvec_small<T, TH, MAXE, GATHER_X, In, Out>;
       set_smem(kern, sm);
+      prof_begin(s);
       kern<<<batch, TH, sm, s>>>(g, x, ldx, y, ldy, chat, off, cnt);
+      prof_end(s, K_MATVEC_SMALL, mv_bytes, mv_flops);
     }
     return;
   }
   cplx<T>* Y = reinterpret_cast<cplx<T>*>(scratch);
-  if (transpose) fs_forward<T, GATHER_XT, In>(g, x, ldx, 0, Y, batch, s);
-  else fs_forward<T, GATHER_X, In>(g, x, ldx, 0, Y, batch, s);
+  if (transpose) fs_forward<T, GATHER_XT, In>(g, x, ldx, 0, Y, batch, s, K_MATVEC_COLFWD, in_b);
+  else fs_forward<T, GATHER_X, In>(g, x, ldx, 0, Y, batch, s, K_MATVEC_COLFWD, in_b);
   RowArgs ra{};
   ra.chat = chat;
-  fs_row<T, ROW_MATVEC>(g, Y, ra, batch, s);
-  fs_inverse<T, OUT_SLICE, Out>(g, Y, y, ldy, off, cnt, 1.0f, batch, s);
+  fs_row<T, ROW_MATVEC>(g, Y, ra, batch, s, K_MATVEC_ROW, spec_b);
+  fs_inverse<T, OUT_SLICE, Out>(g, Y, y, ldy, off, cnt, 1.0f, batch, s, K_MATVEC_COLINV, out_b);
 }
 
 void launch_matvec_df(const Geom& g, int prec, int transpose, const df64* x, int64_t ldx, df64* y, int64_t ldy,
@@ -486,16 +506,18 @@ void launch_spectrum(const Geom& g, const double* f, cplx<df64>* chat, int natur
     const size_t sm = (size_t)(1 << g.lg_n) * sizeof(cplx<df64>);
     auto kern = k_rfft_small<df64, TH, Lim<df64>::MAXE, GATHER_CIRC, double>;
     set_smem(kern, sm);
+    prof_begin(s);
     kern<<<1, TH, sm, s>>>(g, f, 0, 0, chat, 0, scale);
+    prof_end(s, K_SPECTRUM, 8.0 * g.N + 16.0 * (double)((1 << g.lg_n) + 1), 0.0);
     return;
   }
   cplx<df64>* Y = reinterpret_cast<cplx<df64>*>(scratch);
-  fs_forward<df64, GATHER_CIRC, double>(g, f, 0, 0, Y, 1, s);
+  fs_forward<df64, GATHER_CIRC, double>(g, f, 0, 0, Y, 1, s, K_SPECTRUM, 8.0 * g.N);
   RowArgs ra{};
   ra.spec_out = chat;
   ra.natural = natural;
   ra.scale = scale;
-  fs_row<df64, ROW_FWD_STORE>(g, Y, ra, 1, s);
+  fs_row<df64, ROW_FWD_STORE>(g, Y, ra, 1, s, K_SPECTRUM, 16.0 * (double)((1 << g.lg_n) + 1));
 }
 
 template <class T, class Out>
@@ -508,7 +530,9 @@ static void hankel_impl(const Geom& g, const df64* U, int64_t ldu, const df64* V
     const size_t sm = (size_t)(2 << g.lg_n) * sizeof(cplx<T>);
     auto kern = k_hankel_small<T, TH, MAXE, Out>;
     set_smem(kern, sm);
+    prof_begin(s);
     kern<<<m, TH, sm, s>>>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, out, ldo);
+    prof_end(s, K_HANKEL_SMALL, 8.0 * (double)(g.L + g.K) * grp_off_host[m] + 8.0 * (double)g.N * m, 0.0);
     return;
   }
   // large M: per component, forward FFT of u' (stored), forward FFT of v'
@@ -521,24 +545,25 @@ static void hankel_impl(const Geom& g, const df64* U, int64_t ldu, const df64* V
     cudaMemsetAsync(acc, 0, (n + 1) * sizeof(cplx<df64>), s);
     for (int ii = grp_off_host[grp]; ii < grp_off_host[grp + 1]; ++ii) {
       const int comp = grp_idx_host[ii];
-      fs_forward<T, GATHER_PAD, df64>(g, U + (int64_t)comp * ldu, 0, g.L, Y, 1, s);
+      fs_forward<T, GATHER_PAD, df64>(g, U + (int64_t)comp * ldu, 0, g.L, Y, 1, s, K_HANKEL_FS, 8.0 * g.L);
       RowArgs ra{};
       ra.spec_out = su;
       ra.natural = 0;
       ra.scale = 1.0f;
-      fs_row<T, ROW_FWD_STORE>(g, Y, ra, 1, s);
-      fs_forward<T, GATHER_PAD, df64>(g, V + (int64_t)comp * ldv, 0, g.K, Y, 1, s);
+      fs_row<T, ROW_FWD_STORE>(g, Y, ra, 1, s, K_HANKEL_FS, 0.0);
+      fs_forward<T, GATHER_PAD, df64>(g, V + (int64_t)comp * ldv, 0, g.K, Y, 1, s, K_HANKEL_FS, 8.0 * g.K);
       RowArgs rb{};
       rb.spec_in = su;
       rb.spec_out = acc;
       rb.weight = sigma;
       rb.weight_idx = comp;
-      fs_row<T, ROW_FWD_MUL_ACC>(g, Y, rb, 1, s);
+      fs_row<T, ROW_FWD_MUL_ACC>(g, Y, rb, 1, s, K_HANKEL_FS, 0.0);
     }
     RowArgs rc{};
     rc.spec_in = acc;
-    fs_row<T, ROW_INV_LOAD>(g, Y, rc, 1, s);
-    fs_inverse<T, OUT_HANKEL, Out>(g, Y, out + (int64_t)grp * ldo, 0, 0, 0, 1.0f / (2.0f * (float)n), 1, s);
+    fs_row<T, ROW_INV_LOAD>(g, Y, rc, 1, s, K_HANKEL_FS, 0.0);
+    fs_inverse<T, OUT_HANKEL, Out>(g, Y, out + (int64_t)grp * ldo, 0, 0, 0, 1.0f / (2.0f * (float)n), 1, s, K_HANKEL_FS,
+                               8.0 * (double)g.N);
   }
 }
 
