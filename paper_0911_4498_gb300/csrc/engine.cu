@@ -178,6 +178,8 @@ struct Workspace {
     cudaFree(B);
     cudaFree(y);
     cudaFree(rw.part);
+    cudaFree(rw.part2);
+    cudaFree(rw.coop);
     cudaFree(rw.h);
     cudaFree(rw.nrm);
     cudaFree(rw.counter);
@@ -240,7 +242,7 @@ struct ssa_decomp_s {
 namespace ssa {
 static const char* const kClassNames[K_NCLASS] = {
     "spectrum", "matvec_small", "matvec_colfwd", "matvec_row", "matvec_colinv", "cgs_proj", "cgs_update",
-    "normalize", "small_svd", "ritz", "hankel_small", "hankel_fourstep", "misc", "gated"};
+    "cgs_update_proj", "normalize", "small_svd", "ritz", "hankel_small", "hankel_fourstep", "misc", "gated"};
 struct PendingLaunch {
   int cls;
   cudaEvent_t a, b;
@@ -562,6 +564,10 @@ static int ensure_workspace(ssa_plan_t p, int d) {
   CK(cudaMalloc(&w.y, (size_t)((dimmax + 3) / 4 * 4) * sizeof(df64)));
   w.rw.ldp = MAXCOL + 1;
   CK(cudaMalloc(&w.rw.part, (size_t)G * w.rw.ldp * sizeof(df64)));
+  w.rw.ldp2 = FUSED_MAXCOL + 1;
+  CK(cudaMalloc(&w.rw.part2, (size_t)fused_tiles(dimmax) * w.rw.ldp2 * sizeof(df64)));
+  reorth_setup();
+  CK(cudaMalloc(&w.rw.coop, (size_t)coop_blocks() * (MAXCOL + 1) * sizeof(df64)));
   CK(cudaMalloc(&w.rw.h, (MAXCOL + 1) * sizeof(df64)));
   CK(cudaMalloc(&w.rw.nrm, sizeof(df64)));
   CK(cudaMalloc(&w.rw.counter, sizeof(int)));
@@ -644,7 +650,8 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   // p_0 (Algorithm 1, line 1): seeded uniform(-1, 1), normalised into u_1
   launch_random_fill(w.y, Lw, seed, stream_id++, s);
   launch_cgs2(U, w.ldu, 0, w.y, Lw, w.rw, nullptr, s);
-  launch_normalize(w.y, Lw, w.rw, U, w.dummy, w.est, w.flag, 0, seed, stream_id++, w.status, s);
+  CK((cudaError_t)launch_normalize_coop(w.y, Lw, w.rw, U, w.dummy, w.est, U, w.ldu, 0, seed, stream_id++, w.status,
+                                        s));
   CHECK_LAUNCH();
   int r = 1, c = 0;
   auto side = [&](bool vside) -> int {
@@ -659,9 +666,8 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     ++matvecs;
     launch_cgs2(Qb, ldq, ncols, w.y, dim, w.rw, nullptr, s);
     df64* qcol = Qb + (int64_t)ncols * ldq;
-    launch_normalize(w.y, dim, w.rw, qcol, bentry, w.est, w.flag, 0, seed, stream_id, w.status, s);
-    launch_cgs2(Qb, ldq, ncols, w.y, dim, w.rw, w.flag, s);
-    launch_normalize(w.y, dim, w.rw, qcol, bentry, w.est, w.flag, 1, seed, stream_id, w.status, s);
+    CK((cudaError_t)launch_normalize_coop(w.y, dim, w.rw, qcol, bentry, w.est, Qb, ldq, ncols, seed, stream_id,
+                                          w.status, s));
     ++stream_id;
     CHECK_LAUNCH();
     if (vside) ++c;

@@ -9,13 +9,19 @@ constexpr int RP = 4;                // row pairs per thread
 constexpr int SLAB = 2 * RT * RP;    // rows per block
 constexpr int MAXCOL = 512;          // largest basis size (Krylov dimension + 1)
 constexpr int SVD_THREADS = 512;
+constexpr int PRE_THREADS = 1024;
+constexpr int PRE_SMEM_MAX = 200 * 1024;  // FP32 preconditioning of the projected SVD when r*c + c*c floats fit
+constexpr int FUSED_MAXCOL = 200;   // largest basis for the fused update+projection pass
 
 struct ReorthWork {
-  df64* part;    // [blocks][ldp] partial sums
+  df64* part;    // [blocks][ldp] partial sums (row tiles of SLAB rows)
+  df64* part2;   // [tiles][ldp] partial sums of the fused pass (tiles of 64 rows)
   int ldp;
+  int ldp2;      // leading dimension of part2 (FUSED_MAXCOL + 1)
   df64* h;       // projection coefficients (MAXCOL + 1)
   df64* nrm;     // squared norm after the last update
   int* counter;  // last-block counter (returns to 0 after each kernel)
+  df64* coop;    // [coop_blocks()][MAXCOL + 1] scratch of the breakdown branch
 };
 
 struct SvdWork {
@@ -28,10 +34,16 @@ struct SvdWork {
 };
 
 int reorth_blocks(int64_t dim);
+int fused_tiles(int64_t dim);
+void reorth_setup();
 void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, const int* flag,
                  cudaStream_t s);
 void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est, int* flag, int mode,
                       uint64_t seed, uint64_t stream, unsigned* status, cudaStream_t s);
+int coop_blocks();
+int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est,
+                          const df64* Q, int64_t ldq, int ncols, uint64_t seed, uint64_t stream, unsigned* status,
+                          cudaStream_t s);
 void launch_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stream, cudaStream_t s);
 void launch_small_svd(const df64* B, int ldb, int r, int c, const int2* sched, SvdWork& sw, int k, double tol_conv,
                       df64* est, unsigned* status, cudaStream_t s);

@@ -43,12 +43,37 @@ SSA_D bool last_block(int* counter) {
 }
 
 // ---------------------------------------------------------------- CGS pieces
-// h[i] = Q[:, i] . w for i < ncols and h[ncols] = w . w
-__global__ void __launch_bounds__(RT) k_proj(const df64* __restrict__ Q, int64_t ldq, int ncols,
-                                             const df64* __restrict__ w, int64_t dim, df64* __restrict__ part,
-                                             int ldp, df64* __restrict__ hout, int* counter, const int* flag) {
+// Classical Gram-Schmidt applied twice, in three passes over the basis Q
+// (dim x ncols, column-major):
+//   P1  h1 = Q^T w                     (k_cgs_proj, partial sums per row tile)
+//   P2  w' = w - Q h1, h2 = Q^T w'     (k_cgs_update_proj, tile staged in smem)
+//   P3  w'' = w' - Q h2, ||w''||^2     (k_cgs_update)
+// Partial sums over row tiles are reduced by k_reduce_cols in tile order.
+
+// 4-value warp butterfly: on return lane 8*c holds the warp sum of v[c].
+SSA_D df64 warp_sum4_df(df64 v0, df64 v1, df64 v2, df64 v3) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8;
+  df64 sa = b4 ? v0 : v2, sb = b4 ? v1 : v3;
+  df64 ka = b4 ? v2 : v0, kb = b4 ? v3 : v1;
+  df64 x0 = df_add(ka, shfl_xor_df(sa, 16));
+  df64 x1 = df_add(kb, shfl_xor_df(sb, 16));
+  df64 snd = b3 ? x0 : x1, kp = b3 ? x1 : x0;
+  df64 u = df_add(kp, shfl_xor_df(snd, 8));
+  u = df_add(u, shfl_xor_df(u, 4));
+  u = df_add(u, shfl_xor_df(u, 2));
+  u = df_add(u, shfl_xor_df(u, 1));
+  return u;
+}
+
+// P1: part[tile][i] = sum over the tile's rows of Q[:, i] w for i < ncols,
+// and part[tile][ncols] = w.w.  Columns go in batches of 4 so each thread has
+// 16 independent 16-byte loads in flight.
+__global__ void __launch_bounds__(RT) k_cgs_proj(const df64* __restrict__ Q, int64_t ldq, int ncols,
+                                                 const df64* __restrict__ w, int64_t dim, df64* __restrict__ part,
+                                                 int ldp, const int* flag) {
   if (flag && *flag == 0) return;
-  __shared__ df64 red[RT / 32][MAXCOL + 1];
+  __shared__ df64 red[RT / 32][MAXCOL + 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * SLAB;
   df64 wv[RP][2];
@@ -59,26 +84,31 @@ __global__ void __launch_bounds__(RT) k_proj(const df64* __restrict__ Q, int64_t
     wv[p][0] = make_df(v.x, v.y);
     wv[p][1] = make_df(v.z, v.w);
   }
-  for (int i = 0; i <= ncols; ++i) {
-    df64 acc = df_zero();
-    if (i < ncols) {
-      const df64* q = Q + (int64_t)i * ldq;
+  for (int c0 = 0; c0 <= ncols; c0 += 4) {
+    float4 q[4][RP];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int col = c0 + b;
 #pragma unroll
       for (int p = 0; p < RP; ++p) {
         const int64_t row = r0 + 2 * ((int64_t)threadIdx.x + p * RT);
-        float4 v = ld_pair(q, row, dim);
-        acc = df_fma(make_df(v.x, v.y), wv[p][0], acc);
-        acc = df_fma(make_df(v.z, v.w), wv[p][1], acc);
-      }
-    } else {
-#pragma unroll
-      for (int p = 0; p < RP; ++p) {
-        acc = df_fma(wv[p][0], wv[p][0], acc);
-        acc = df_fma(wv[p][1], wv[p][1], acc);
+        if (col < ncols) q[b][p] = ld_pair(Q + (int64_t)col * ldq, row, dim);
+        else if (col == ncols) q[b][p] = make_float4(wv[p][0].hi, wv[p][0].lo, wv[p][1].hi, wv[p][1].lo);
+        else q[b][p] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    acc = warp_sum_df(acc);
-    if (lane == 0) red[warp][i] = acc;
+    df64 acc[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      acc[b] = df_zero();
+#pragma unroll
+      for (int p = 0; p < RP; ++p) {
+        acc[b] = df_fma(make_df(q[b][p].x, q[b][p].y), wv[p][0], acc[b]);
+        acc[b] = df_fma(make_df(q[b][p].z, q[b][p].w), wv[p][1], acc[b]);
+      }
+    }
+    const df64 u = warp_sum4_df(acc[0], acc[1], acc[2], acc[3]);
+    if ((lane & 7) == 0) red[warp][c0 + (lane >> 3)] = u;
   }
   __syncthreads();
   for (int i = threadIdx.x; i <= ncols; i += RT) {
@@ -87,26 +117,87 @@ __global__ void __launch_bounds__(RT) k_proj(const df64* __restrict__ Q, int64_t
     for (int wp = 0; wp < RT / 32; ++wp) s = df_add(s, red[wp][i]);
     part[(int64_t)blockIdx.x * ldp + i] = s;
   }
-  if (last_block(counter)) {
-    for (int i = threadIdx.x; i <= ncols; i += RT) {
-      df64 s = df_zero();
-      for (int b = 0; b < (int)gridDim.x; ++b) {
-        const volatile df64* pp = part + (int64_t)b * ldp + i;
-        s = df_add(s, make_df(pp->hi, pp->lo));
-      }
-      hout[i] = s;
+}
+
+// out[i] = sum_t part[t][i] for i < ncols (tile order, one warp per column)
+__global__ void k_reduce_cols(const df64* __restrict__ part, int ntiles, int ldp, int ncols, df64* __restrict__ out,
+                              const int* flag) {
+  if (flag && *flag == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  df64 s = df_zero();
+  for (int t = lane; t < ntiles; t += 32) s = df_add(s, part[(int64_t)t * ldp + col]);
+  s = warp_sum_df(s);
+  if (lane == 0) out[col] = s;
+}
+
+// P2: w' = w - Q h over a tile of FR rows held in shared memory with all
+// ncols columns, then part[tile][i] = Q[tile, i] . w'[tile] and
+// part[tile][ncols] = w'.w'.
+constexpr int FR = 64;
+constexpr int FRP = FR + 1;  // padded column stride in shared memory
+__global__ void __launch_bounds__(256) k_cgs_update_proj(const df64* __restrict__ Q, int64_t ldq, int ncols,
+                                                         df64* __restrict__ w, int64_t dim,
+                                                         const df64* __restrict__ h, df64* __restrict__ part,
+                                                         int ldp, const int* flag) {
+  if (flag && *flag == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  df64* Qs = reinterpret_cast<df64*>(smem_raw);  // [ncols][FRP]
+  df64* ws = Qs + (size_t)ncols * FRP;             // [FR]
+  df64* hs = ws + FR;                              // [ncols]
+  const int64_t r0 = (int64_t)blockIdx.x * FR;
+  for (int e = threadIdx.x; e < ncols * (FR / 2); e += 256) {
+    const int c = e / (FR / 2), l = e - c * (FR / 2);
+    const float4 v = ld_pair(Q + (int64_t)c * ldq, r0 + 2 * l, dim);
+    Qs[c * FRP + 2 * l] = make_df(v.x, v.y);
+    Qs[c * FRP + 2 * l + 1] = make_df(v.z, v.w);
+  }
+  if (threadIdx.x < FR / 2) {
+    const float4 v = ld_pair(w, r0 + 2 * threadIdx.x, dim);
+    ws[2 * threadIdx.x] = make_df(v.x, v.y);
+    ws[2 * threadIdx.x + 1] = make_df(v.z, v.w);
+  }
+  for (int c = threadIdx.x; c < ncols; c += 256) hs[c] = h[c];
+  __syncthreads();
+  {  // w' rows: 4 threads per row split the columns
+    const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+    df64 acc = df_zero();
+    for (int c = q; c < ncols; c += 4) acc = df_fma(Qs[c * FRP + r], hs[c], acc);
+    acc = df_add(acc, shfl_xor_df(acc, 1));
+    acc = df_add(acc, shfl_xor_df(acc, 2));
+    __syncthreads();
+    if (q == 0) {
+      const df64 x = (r0 + r < dim) ? df_sub(ws[r], acc) : df_zero();
+      ws[r] = x;
+      if (r0 + r < dim) w[r0 + r] = x;
     }
-    if (threadIdx.x == 0) *counter = 0;
+  }
+  __syncthreads();
+  // projections of w' on every column (and w'.w'), two threads per column
+  // every thread runs the same number of iterations so the shuffle sees a full warp
+  const int tot = 2 * (ncols + 1);
+  for (int e0 = 0; e0 < tot; e0 += 256) {
+    const int e = e0 + threadIdx.x;
+    const int c = e >> 1, half = e & 1;
+    df64 acc = df_zero();
+    if (c <= ncols) {
+      const df64* col = c < ncols ? Qs + c * FRP : ws;
+      for (int r = half * (FR / 2); r < (half + 1) * (FR / 2); ++r) acc = df_fma(col[r], ws[r], acc);
+    }
+    acc = df_add(acc, shfl_xor_df(acc, 1));
+    if (half == 0 && c <= ncols) part[(int64_t)blockIdx.x * ldp + c] = acc;
   }
 }
 
-// w -= Q[:, :ncols] h ; nrm_out = w . w
-__global__ void __launch_bounds__(RT) k_update(const df64* __restrict__ Q, int64_t ldq, int ncols,
-                                               df64* __restrict__ w, int64_t dim, const df64* __restrict__ h,
-                                               df64* __restrict__ part, df64* __restrict__ nrm_out, int* counter,
-                                               const int* flag) {
+// P3: w -= Q h; part[tile] = w.w over the tile; the last block sums the
+// tile partials into *nrm_out.  Columns in batches of 4 for load parallelism.
+__global__ void __launch_bounds__(RT) k_cgs_update(const df64* __restrict__ Q, int64_t ldq, int ncols,
+                                                   df64* __restrict__ w, int64_t dim, const df64* __restrict__ h,
+                                                   df64* __restrict__ part, df64* __restrict__ nrm_out,
+                                                   int* counter, const int* flag) {
   if (flag && *flag == 0) return;
-  __shared__ df64 hs[MAXCOL + 1];
+  __shared__ df64 hs[MAXCOL + 4];
   __shared__ df64 red[RT / 32];
   for (int i = threadIdx.x; i < ncols; i += RT) hs[i] = h[i];
   __syncthreads();
@@ -115,15 +206,31 @@ __global__ void __launch_bounds__(RT) k_update(const df64* __restrict__ Q, int64
   df64 acc[RP][2];
 #pragma unroll
   for (int p = 0; p < RP; ++p) acc[p][0] = acc[p][1] = df_zero();
-  for (int i = 0; i < ncols; ++i) {
-    const df64 hi = hs[i];
-    const df64* q = Q + (int64_t)i * ldq;
+  int c0 = 0;
+  for (; c0 + 4 <= ncols; c0 += 4) {
+    float4 q[4][RP];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int p = 0; p < RP; ++p)
+        q[b][p] = ld_pair(Q + (int64_t)(c0 + b) * ldq, r0 + 2 * ((int64_t)threadIdx.x + p * RT), dim);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const df64 hb = hs[c0 + b];
+#pragma unroll
+      for (int p = 0; p < RP; ++p) {
+        acc[p][0] = df_fma(make_df(q[b][p].x, q[b][p].y), hb, acc[p][0]);
+        acc[p][1] = df_fma(make_df(q[b][p].z, q[b][p].w), hb, acc[p][1]);
+      }
+    }
+  }
+  for (; c0 < ncols; ++c0) {
+    const df64 hb = hs[c0];
 #pragma unroll
     for (int p = 0; p < RP; ++p) {
-      const int64_t row = r0 + 2 * ((int64_t)threadIdx.x + p * RT);
-      float4 v = ld_pair(q, row, dim);
-      acc[p][0] = df_fma(make_df(v.x, v.y), hi, acc[p][0]);
-      acc[p][1] = df_fma(make_df(v.z, v.w), hi, acc[p][1]);
+      const float4 v = ld_pair(Q + (int64_t)c0 * ldq, r0 + 2 * ((int64_t)threadIdx.x + p * RT), dim);
+      acc[p][0] = df_fma(make_df(v.x, v.y), hb, acc[p][0]);
+      acc[p][1] = df_fma(make_df(v.z, v.w), hb, acc[p][1]);
     }
   }
   df64 nrm = df_zero();
@@ -233,6 +340,101 @@ __global__ void k_normalize(df64* __restrict__ w, int64_t dim, const df64* __res
 
 __global__ void k_clear_flag(int* flag) { *flag = 0; }
 
+namespace cg = cooperative_groups;
+
+// Block sum of one df64 per thread; result valid in thread 0.
+SSA_D df64 block_sum_df(df64 v, df64* sh) {
+  v = warp_sum_df(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  df64 s = df_zero();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s = df_add(s, sh[i]);
+  return s;
+}
+
+// Normalise w into qcol and record the coupling coefficient (one cooperative
+// launch).  Usual case: beta = sqrt(nrm2) > 1e-14 * est, qcol = w / beta.
+// Breakdown (beta at or below that level, including 0): the coefficient is
+// recorded as 0 and w is replaced by a seeded random vector, orthogonalised
+// against the ncols basis columns by CGS2 inside the kernel (grid-wide
+// barriers between the passes); if it vanishes the basis already spans the
+// space and qcol is set to zero.  est (largest coupling / singular value
+// seen) is raised by block 0 at the end; other blocks may read the old or
+// the new value, which gives the same decision because the new value is beta.
+__global__ void __launch_bounds__(256) k_normalize_coop(df64* __restrict__ w, int64_t dim,
+                                                        const df64* __restrict__ nrm2, df64* __restrict__ qcol,
+                                                        df64* __restrict__ bentry, df64* est,
+                                                        const df64* __restrict__ Q, int64_t ldq, int ncols,
+                                                        df64* __restrict__ scratch, int lds, uint64_t seed,
+                                                        uint64_t stream, unsigned* status) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  __shared__ df64 sh[32];
+  __shared__ df64 hs[MAXCOL + 4];
+  const df64 beta = df_sqrt(*nrm2);
+  if (!isfinite(beta.hi) && tid == 0) atomicOr(status, SSA_DEV_NONFINITE);
+  const float thr = 1e-14f * est->hi;
+  if (beta.hi > thr && beta.hi > 0.f && isfinite(beta.hi)) {
+    const df64 inv = df_div(make_df(1.f, 0.f), beta);
+    for (int64_t i = tid; i < dim; i += stride) qcol[i] = df_mul(w[i], inv);
+    if (tid == 0) {
+      *bentry = beta;
+      if (df_gt(beta, *est)) *est = beta;
+    }
+    return;
+  }
+  // ---- breakdown: the whole grid takes this branch
+  cg::grid_group grid = cg::this_grid();
+  if (tid == 0) {
+    *bentry = df_zero();
+    atomicOr(status, SSA_DEV_BREAKDOWN);
+  }
+  for (int64_t i = tid; i < dim; i += stride) w[i] = sm64_uniform_pm1(seed, stream, i);
+  for (int pass = 0; pass < 2 && ncols > 0; ++pass) {
+    grid.sync();
+    for (int c = 0; c < ncols; ++c) {
+      const df64* q = Q + (int64_t)c * ldq;
+      df64 a = df_zero();
+      for (int64_t i = tid; i < dim; i += stride) a = df_fma(q[i], w[i], a);
+      a = block_sum_df(a, sh);
+      if (threadIdx.x == 0) scratch[(int64_t)blockIdx.x * lds + c] = a;
+    }
+    grid.sync();
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+      df64 a = df_zero();
+      for (int b = 0; b < (int)gridDim.x; ++b) a = df_add(a, scratch[(int64_t)b * lds + c]);
+      hs[c] = a;
+    }
+    __syncthreads();
+    for (int64_t i = tid; i < dim; i += stride) {
+      df64 a = df_zero();
+      for (int c = 0; c < ncols; ++c) a = df_fma(Q[(int64_t)c * ldq + i], hs[c], a);
+      w[i] = df_sub(w[i], a);
+    }
+  }
+  grid.sync();
+  df64 a = df_zero();
+  for (int64_t i = tid; i < dim; i += stride) a = df_fma(w[i], w[i], a);
+  a = block_sum_df(a, sh);
+  if (threadIdx.x == 0) scratch[(int64_t)blockIdx.x * lds + MAXCOL] = a;
+  grid.sync();
+  if (threadIdx.x == 0) {
+    df64 t = df_zero();
+    for (int b = 0; b < (int)gridDim.x; ++b) t = df_add(t, scratch[(int64_t)b * lds + MAXCOL]);
+    sh[0] = t;
+  }
+  __syncthreads();
+  const df64 nb = df_sqrt(sh[0]);
+  // the random vector had norm ~ sqrt(dim/3) before orthogonalisation
+  const bool alive = nb.hi > 1e-6f * sqrtf((float)dim / 3.f);
+  const df64 inv = alive ? df_div(make_df(1.f, 0.f), nb) : df_zero();
+  for (int64_t i = tid; i < dim; i += stride) qcol[i] = df_mul(w[i], inv);
+}
+
+
 // ---------------------------------------------------------------- projected SVD
 // One-sided Jacobi (Hestenes) on the r x c block of B (row-major, leading
 // dimension ldb), in one CTA.  Parallel ordering: the host supplies a
@@ -248,18 +450,20 @@ __global__ void __launch_bounds__(SVD_THREADS) k_small_svd(const df64* __restric
                                                            df64* __restrict__ Qv, double* __restrict__ resid,
                                                            double* __restrict__ sigma_d, int k, double tol_conv,
                                                            int* conv, df64* est, unsigned* status, int max_sweeps,
-                                                           float rot_tol) {
+                                                           float rot_tol, int warm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = SVD_THREADS / 32;
   __shared__ int rotated;
   __shared__ int sweeps_used;
-  // A = B[:r, :c] in column-major, W = I
-  for (int e = threadIdx.x; e < r * c; e += SVD_THREADS) {
-    const int i = e % r, j = e / r;
-    A[(int64_t)j * r + i] = B[(int64_t)i * ldb + j];
-  }
-  for (int e = threadIdx.x; e < c * c; e += SVD_THREADS) {
-    const int i = e % c, j = e / c;
-    W[(int64_t)j * c + i] = make_df(i == j ? 1.f : 0.f, 0.f);
+  // A = B[:r, :c] in column-major, W = I (unless k_svd_precondition left A = B W, W)
+  if (!warm) {
+    for (int e = threadIdx.x; e < r * c; e += SVD_THREADS) {
+      const int i = e % r, j = e / r;
+      A[(int64_t)j * r + i] = B[(int64_t)i * ldb + j];
+    }
+    for (int e = threadIdx.x; e < c * c; e += SVD_THREADS) {
+      const int i = e % c, j = e / c;
+      W[(int64_t)j * c + i] = make_df(i == j ? 1.f : 0.f, 0.f);
+    }
   }
   if (threadIdx.x == 0) sweeps_used = -1;
   __syncthreads();
@@ -380,6 +584,108 @@ __global__ void __launch_bounds__(SVD_THREADS) k_small_svd(const df64* __restric
   }
 }
 
+// Preconditioning of the projected SVD (one CTA):
+//   1. one-sided Jacobi in FP32 on the rounded r x c block of B, in shared
+//      memory, to orthogonality ~1e-6 (cheap sweeps on the FP32 pipes);
+//   2. its right rotations W32, widened to df64, re-orthogonalised by one
+//      Newton-Schulz step W <- W (3I - W^T W) / 2 (quadratic: 1e-7 -> 1e-14);
+//   3. A = B W in df64.
+// k_small_svd then finishes with df64 sweeps from (A, W), which converge in
+// about two sweeps because A's columns are already nearly orthogonal.
+// T1 is a c x c df64 scratch array.
+__global__ void __launch_bounds__(PRE_THREADS) k_svd_precondition(const df64* __restrict__ B, int ldb, int r, int c,
+                                                                  df64* __restrict__ A, df64* __restrict__ W,
+                                                                  df64* __restrict__ T1,
+                                                                  const int2* __restrict__ sched, int cc,
+                                                                  int max_sweeps, float tol32) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* A32 = reinterpret_cast<float*>(smem_raw);  // r x c
+  float* W32 = A32 + (size_t)r * c;                 // c x c
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = PRE_THREADS / 32;
+  __shared__ int rotated;
+  for (int e = threadIdx.x; e < r * c; e += PRE_THREADS) {
+    const int i = e % r, j = e / r;
+    const df64 b = B[(int64_t)i * ldb + j];
+    A32[j * r + i] = b.hi + b.lo;
+  }
+  for (int e = threadIdx.x; e < c * c; e += PRE_THREADS) W32[e] = (e % c == e / c) ? 1.f : 0.f;
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < cc - 1; ++rnd) {
+      for (int pr = warp; pr < cc / 2; pr += nw) {
+        const int2 pq = sched[(int64_t)rnd * (cc / 2) + pr];
+        const int p = pq.x, q = pq.y;
+        if (p >= c || q >= c) continue;
+        float* ap = A32 + p * r;
+        float* aq = A32 + q * r;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int i = lane; i < r; i += 32) {
+          const float x = ap[i], y = aq[i];
+          al = fmaf(x, x, al);
+          be = fmaf(y, y, be);
+          ga = fmaf(x, y, ga);
+        }
+#pragma unroll
+        for (int m = 16; m; m >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, m);
+          be += __shfl_xor_sync(0xffffffffu, be, m);
+          ga += __shfl_xor_sync(0xffffffffu, ga, m);
+        }
+        if (!(al > 0.f) || !(be > 0.f)) continue;
+        if (!(fabsf(ga) > tol32 * sqrtf(al) * sqrtf(be))) continue;
+        const float zeta = (be - al) / (2.f * ga);
+        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float cs = 1.f / sqrtf(1.f + t * t);
+        const float sn = cs * t;
+        for (int i = lane; i < r; i += 32) {
+          const float x = ap[i], y = aq[i];
+          ap[i] = cs * x - sn * y;
+          aq[i] = sn * x + cs * y;
+        }
+        float* wp = W32 + p * c;
+        float* wq = W32 + q * c;
+        for (int i = lane; i < c; i += 32) {
+          const float x = wp[i], y = wq[i];
+          wp[i] = cs * x - sn * y;
+          wq[i] = sn * x + cs * y;
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  // T1 = W32^T W32 (exact products of floats, df64 sums); W = W32 (1.5 I - 0.5 T1)
+  for (int e = threadIdx.x; e < c * c; e += PRE_THREADS) {
+    const int i = e % c, j = e / c;
+    const float* wi = W32 + i * c;
+    const float* wj = W32 + j * c;
+    df64 a = df_zero();
+    for (int k = 0; k < c; ++k) a = df_add(a, two_prod(wi[k], wj[k]));
+    T1[(int64_t)j * c + i] = a;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < c * c; e += PRE_THREADS) {
+    const int row = e % c, j = e / c;
+    df64 a = df_zero();
+    for (int i = 0; i < c; ++i) a = df_fma(make_df(W32[i * c + row], 0.f), T1[(int64_t)j * c + i], a);
+    const df64 wkj = make_df(W32[j * c + row], 0.f);
+    W[(int64_t)j * c + row] = df_sub(df_mul_f(wkj, 1.5f), df_scale(a, 0.5f));
+  }
+  __syncthreads();
+  // A = B[:r, :c] W (df64)
+  for (int e = threadIdx.x; e < r * c; e += PRE_THREADS) {
+    const int i = e % r, j = e / r;
+    df64 a = df_zero();
+    for (int k = 0; k < c; ++k) a = df_fma(B[(int64_t)i * ldb + k], W[(int64_t)j * c + k], a);
+    A[(int64_t)j * r + i] = a;
+  }
+}
+
 // Thick restart: B <- [diag(sigma_1..sigma_kk) | rho], rho_i = alpha_res P[r-1, i].
 __global__ void k_restart_B(df64* B, int ldb, int nrows_clear, const df64* __restrict__ sigma,
                             const df64* __restrict__ P, int r, int kk, df64 alpha_res_unused, int c_old) {
@@ -496,29 +802,53 @@ static int grid_for(int64_t n, int threads, int cap) {
 }
 
 int reorth_blocks(int64_t dim) { return (int)((dim + SLAB - 1) / SLAB); }
+int fused_tiles(int64_t dim) { return (int)((dim + FR - 1) / FR); }
 
 // CGS2: w <- (I - Q Q^T)^2 w, nrm2 <- ||w||^2.  flag (may be null) gates the
 // whole sequence on the device (used for the breakdown replacement).
 void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, const int* flag,
                  cudaStream_t s) {
   const int G = reorth_blocks(dim);
-  // algorithmic bytes: the ncols basis columns once, w read (and written by the update)
+  // algorithmic bytes: the ncols basis columns once per pass, w read (and written by updates)
   const double qb = 8.0 * (double)dim * ncols;
   const double fl = 2.0 * (double)dim * ncols;
+  const int gated = flag ? 1 : 0;
   if (ncols > 0) {
     prof_begin(s);
-    k_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, rw.h, rw.counter, flag);
-    prof_end(s, flag ? K_GATED : K_PROJ, flag ? 0.0 : qb + 8.0 * dim, flag ? 0.0 : fl);
+    k_cgs_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, flag);
+    prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
     prof_begin(s);
-    k_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
-    prof_end(s, flag ? K_GATED : K_UPDATE, flag ? 0.0 : qb + 16.0 * dim, flag ? 0.0 : fl);
-    prof_begin(s);
-    k_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, rw.h, rw.counter, flag);
-    prof_end(s, flag ? K_GATED : K_PROJ, flag ? 0.0 : qb + 8.0 * dim, flag ? 0.0 : fl);
+    k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part, G, rw.ldp, ncols, rw.h, flag);
+    prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+    const int T2 = (int)((dim + FR - 1) / FR);
+    if (ncols <= FUSED_MAXCOL) {
+      const size_t sm = ((size_t)ncols * FRP + FR + ncols) * sizeof(df64);
+      prof_begin(s);
+      k_cgs_update_proj<<<T2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, rw.ldp2, flag);
+      prof_end(s, gated ? K_GATED : K_UPDATE_PROJ, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : 2 * fl);
+      prof_begin(s);
+      k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part2, T2, rw.ldp2, ncols, rw.h, flag);
+      prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+    } else {
+      prof_begin(s);
+      k_cgs_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
+      prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
+      prof_begin(s);
+      k_cgs_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, flag);
+      prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
+      prof_begin(s);
+      k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part, G, rw.ldp, ncols, rw.h, flag);
+      prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+    }
   }
   prof_begin(s);
-  k_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
-  prof_end(s, flag ? K_GATED : K_UPDATE, flag ? 0.0 : qb + 16.0 * dim, flag ? 0.0 : fl);
+  k_cgs_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
+  prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
+}
+
+void reorth_setup() {
+  cudaFuncSetAttribute(k_cgs_update_proj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(((size_t)FUSED_MAXCOL * FRP + FR + FUSED_MAXCOL) * sizeof(df64)));
 }
 
 void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est, int* flag, int mode,
@@ -527,6 +857,34 @@ void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* be
   k_normalize<<<grid_for(dim, 256, 1184), 256, 0, s>>>(w, dim, rw.nrm, qcol, bentry, est, flag, mode, seed, stream,
                                                        status);
   prof_end(s, mode == 0 ? K_NORMALIZE : K_GATED, mode == 0 ? 16.0 * dim : 0.0, 0.0);
+}
+
+static int g_coop_blocks = 0;
+int coop_blocks() {
+  if (g_coop_blocks == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_normalize_coop, 256, 0);
+    if (per < 1) per = 1;
+    if (per > 4) per = 4;
+    g_coop_blocks = sms * per;
+  }
+  return g_coop_blocks;
+}
+
+int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est,
+                          const df64* Q, int64_t ldq, int ncols, uint64_t seed, uint64_t stream, unsigned* status,
+                          cudaStream_t s) {
+  int blocks = grid_for(dim, 256, coop_blocks());
+  int lds = MAXCOL + 1;
+  const df64* nrm = rw.nrm;
+  df64* scratch = rw.coop;
+  void* args[] = {&w, &dim, &nrm, &qcol, &bentry, &est, &Q, &ldq, &ncols, &scratch, &lds, &seed, &stream, &status};
+  prof_begin(s);
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_normalize_coop, dim3(blocks), dim3(256), args, 0, s);
+  prof_end(s, K_NORMALIZE, 16.0 * dim, 0.0);
+  return e == cudaSuccess ? 0 : (int)e;
 }
 
 void launch_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stream, cudaStream_t s) {
@@ -538,9 +896,23 @@ void launch_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stream, cu
 void launch_small_svd(const df64* B, int ldb, int r, int c, const int2* sched, SvdWork& sw, int k, double tol_conv,
                       df64* est, unsigned* status, cudaStream_t s) {
   const int cc = c + (c & 1);
+  const size_t pre_sm = ((size_t)r * c + (size_t)c * c) * sizeof(float);
+  int warm = 0;
+  if (c >= 16 && pre_sm <= (size_t)PRE_SMEM_MAX) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_svd_precondition, cudaFuncAttributeMaxDynamicSharedMemorySize, PRE_SMEM_MAX);
+      attr = true;
+    }
+    prof_begin(s);
+    k_svd_precondition<<<1, PRE_THREADS, pre_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, sched, cc, 40, 2e-6f);
+    prof_end(s, K_SMALL_SVD, 0.0, 0.0);
+    warm = 1;
+  }
   prof_begin(s);
   k_small_svd<<<1, SVD_THREADS, 0, s>>>(B, ldb, r, c, sw.A, sw.W, sched, cc, sw.sigma, sw.P, sw.Q, sw.resid,
-                                         sw.sigma_d, k, tol_conv, sw.conv, est, status, sw.max_sweeps, sw.rot_tol);
+                                         sw.sigma_d, k, tol_conv, sw.conv, est, status, sw.max_sweeps, sw.rot_tol,
+                                         warm);
   prof_end(s, K_SMALL_SVD, 0.0, 0.0);
 }
 

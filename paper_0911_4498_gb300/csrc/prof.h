@@ -15,6 +15,7 @@ enum KClass {
   K_MATVEC_COLINV,
   K_PROJ,
   K_UPDATE,
+  K_UPDATE_PROJ,
   K_NORMALIZE,
   K_SMALL_SVD,
   K_RITZ,

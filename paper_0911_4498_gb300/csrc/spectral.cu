@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(THREADS) k_matvec_small(Geom g, const In* __re
   cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n, 1, g.tw, g.lg_P);
   for (int k = threadIdx.x; k <= n / 2; k += THREADS) {
     const int nk = (n - k) & (n - 1);
-    cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, k) : c_one<T>();
+    cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
     cplx<T> wk, wnk, zk, znk;
     rfft_post(buf[k], buf[nk], tw, wk, wnk);
     cplx<T> pk = mul_spec(wk, chat[k]);
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(THREADS) k_rfft_small(Geom g, const In* __rest
   const float s = 0.5f * scale;
   for (int k = threadIdx.x; k <= n / 2; k += THREADS) {
     const int nk = (n - k) & (n - 1);
-    cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, k) : c_one<T>();
+    cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
     cplx<T> wk, wnk;
     rfft_post(buf[k], buf[nk], tw, wk, wnk);
     wk = c_scale(wk, s);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(THREADS) k_hankel_small(Geom g, const df64* __
       const int k = threadIdx.x + q * THREADS;
       if (k <= n / 2) {
         const int nk = (n - k) & (n - 1);
-        cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, k) : c_one<T>();
+        cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
         cplx<T> uk, unk, vk, vnk;
         rfft_post(bu[k], bu[nk], tw, uk, unk);
         rfft_post(bv[k], bv[nk], tw, vk, vnk);
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(THREADS) k_hankel_small(Geom g, const df64* __
     const int k = threadIdx.x + q * THREADS;
     if (k <= n / 2) {
       const int nk = (n - k) & (n - 1);
-      cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, k) : c_one<T>();
+      cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
       cplx<T> zk, znk;
       irfft_pre(acc_k[q], acc_nk[q], tw, zk, znk);
       bu[k] = zk;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(THREADS) k_fs_col_fwd(Geom g, const In* __rest
     const int64_t b = b0 + bb;
     cplx<T> v = buf[(bb << g.lg_n1) + c];
     const int64_t m = (2 * ((b * c) & (n - 1)));
-    if (m) v = c_mul(v, twiddle_M<T>(g.tA, g.tB, g.tws, m));
+    if (m) v = c_mul(v, twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(m) << g.twshift));
     Y[((int64_t)c << g.lg_n2) + b] = v;
   }
   (void)n1;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict_
     // perm-layout positions (row-major c * n2 + e); the partner of k = 0 is index n
     const int64_t pa = ((int64_t)ca << g.lg_n2) + ea;
     const int64_t pb = k0 ? n : ((int64_t)cbr << g.lg_n2) + eb;
-    cplx<T> tw = k0 ? c_one<T>() : twiddle_M<T>(g.tA, g.tB, g.tws, k);
+    cplx<T> tw = k0 ? c_one<T>() : twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift);
     cplx<T> pk, pnk;
     if (MODE == ROW_INV_LOAD) {
       const cplx<df64> a = sin_[pa], b = sin_[pb];
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict_
     const int64_t b = e & (n2 - 1);
     cplx<T> v = buf[e];
     const int64_t m = 2 * ((b * row) & (n - 1));
-    if (m) v = c_mul_conj(v, twiddle_M<T>(g.tA, g.tB, g.tws, m));
+    if (m) v = c_mul_conj(v, twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(m) << g.twshift));
     Y[((int64_t)row << g.lg_n2) + b] = v;
   }
 }
@@ -371,10 +371,14 @@ static int lg2(int64_t x) {
   return r;
 }
 
+// MAXE: largest single-CTA transform (128 KB of shared memory, 512 threads);
+// COLE: elements per CTA of the four-step column kernels (32 KB, 256 threads),
+// small enough for several CTAs per SM and no register spills.
 template <class T> struct Lim;
-template <> struct Lim<float> { static constexpr int MAXE = 16384; };
-template <> struct Lim<df64> { static constexpr int MAXE = 8192; };
+template <> struct Lim<float> { static constexpr int MAXE = 16384; static constexpr int COLE = 4096; };
+template <> struct Lim<df64> { static constexpr int MAXE = 8192; static constexpr int COLE = 2048; };
 constexpr int TH = 512;
+constexpr int TH_COL = 256;
 constexpr int TH_ROW = 256;
 constexpr int MAXE_ROW = 4096;
 
@@ -406,14 +410,14 @@ int col_lg_cb(const Geom& g, int maxe) {
 template <class T, int G, class In>
 static void fs_forward(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s,
                        int cls, double bytes) {
-  constexpr int MAXE = Lim<T>::MAXE;
+  constexpr int MAXE = Lim<T>::COLE;
   const int lg_cb = col_lg_cb(g, MAXE);
   const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
-  auto kern = k_fs_col_fwd<T, TH, MAXE, G, In>;
+  auto kern = k_fs_col_fwd<T, TH_COL, MAXE, G, In>;
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
   prof_begin(s);
-  kern<<<grid, TH, sm, s>>>(g, x, ldx, glen, Y, lg_cb);
+  kern<<<grid, TH_COL, sm, s>>>(g, x, ldx, glen, Y, lg_cb);
   prof_end(s, cls, bytes, 5.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n1 * batch, 1);
 }
 
@@ -431,14 +435,14 @@ static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cuda
 template <class T, int OUTM, class Out>
 static void fs_inverse(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int64_t off, int64_t cnt, float scale,
                        int batch, cudaStream_t s, int cls, double bytes) {
-  constexpr int MAXE = Lim<T>::MAXE;
+  constexpr int MAXE = Lim<T>::COLE;
   const int lg_cb = col_lg_cb(g, MAXE);
   const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
-  auto kern = k_fs_col_inv<T, TH, MAXE, OUTM, Out>;
+  auto kern = k_fs_col_inv<T, TH_COL, MAXE, OUTM, Out>;
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
   prof_begin(s);
-  kern<<<grid, TH, sm, s>>>(g, Y, y, ldy, off, cnt, scale, lg_cb);
+  kern<<<grid, TH_COL, sm, s>>>(g, Y, y, ldy, off, cnt, scale, lg_cb);
   prof_end(s, cls, bytes, 5.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n1 * batch, 1);
 }
 

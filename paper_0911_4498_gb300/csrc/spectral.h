@@ -21,6 +21,7 @@ struct Geom {
   const cplx<df64>* tA;
   const cplx<df64>* tB;
   int tws;
+  int twshift;  // the two-level table is for M << twshift (batched series share the largest table)
 };
 
 struct RowArgs {
