@@ -132,62 +132,126 @@ __global__ void k_reduce_cols(const df64* __restrict__ part, int ntiles, int ldp
   if (lane == 0) out[col] = s;
 }
 
-// P2: w' = w - Q h over a tile of FR rows held in shared memory with all
-// ncols columns, then part[tile][i] = Q[tile, i] . w'[tile] and
-// part[tile][ncols] = w'.w'.
+// Asynchronous 16-byte global->shared copies (LDGSTS); a copy with
+// valid == false writes zeros and reads nothing.
+SSA_D void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+SSA_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> SSA_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Tile-walking CGS pass over Q (dim x ncols, ncols <= FUSED_MAXCOL):
+//   UPD:  w <- w - Q h          (h read from memory)
+//   PROJ: part[block][c] = sum over the block's tiles of Q[tile, c] . w[tile]
+//   always: part[block][ncols] = sum of w.w over the block's tiles (after UPD)
+// Persistent blocks walk tiles of FR rows; each tile (all ncols columns and the
+// w rows) is copied to shared memory asynchronously and double-buffered, so
+// many 16-byte copies are in flight per SM without holding registers.  The
+// projections accumulate per (column, half-tile) thread across tiles, so a
+// block writes one partial row.
 constexpr int FR = 64;
-constexpr int FRP = FR + 1;  // padded column stride in shared memory
-__global__ void __launch_bounds__(256) k_cgs_update_proj(const df64* __restrict__ Q, int64_t ldq, int ncols,
-                                                         df64* __restrict__ w, int64_t dim,
-                                                         const df64* __restrict__ h, df64* __restrict__ part,
-                                                         int ldp, const int* flag) {
+constexpr int FRP = 66;  // column stride in shared memory (16-byte aligned, fewer bank conflicts)
+template <bool UPD, bool PROJ>
+__global__ void __launch_bounds__(256) k_cgs_tiles(const df64* __restrict__ Q, int64_t ldq, int ncols,
+                                                   df64* __restrict__ w, int64_t dim, const df64* __restrict__ h,
+                                                   df64* __restrict__ part, int ldp, int ntiles, const int* flag) {
   if (flag && *flag == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  df64* Qs = reinterpret_cast<df64*>(smem_raw);  // [ncols][FRP]
-  df64* ws = Qs + (size_t)ncols * FRP;             // [FR]
-  df64* hs = ws + FR;                              // [ncols]
-  const int64_t r0 = (int64_t)blockIdx.x * FR;
-  for (int e = threadIdx.x; e < ncols * (FR / 2); e += 256) {
-    const int c = e / (FR / 2), l = e - c * (FR / 2);
-    const float4 v = ld_pair(Q + (int64_t)c * ldq, r0 + 2 * l, dim);
-    Qs[c * FRP + 2 * l] = make_df(v.x, v.y);
-    Qs[c * FRP + 2 * l + 1] = make_df(v.z, v.w);
-  }
-  if (threadIdx.x < FR / 2) {
-    const float4 v = ld_pair(w, r0 + 2 * threadIdx.x, dim);
-    ws[2 * threadIdx.x] = make_df(v.x, v.y);
-    ws[2 * threadIdx.x + 1] = make_df(v.z, v.w);
-  }
-  for (int c = threadIdx.x; c < ncols; c += 256) hs[c] = h[c];
-  __syncthreads();
-  {  // w' rows: 4 threads per row split the columns
-    const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
-    df64 acc = df_zero();
-    for (int c = q; c < ncols; c += 4) acc = df_fma(Qs[c * FRP + r], hs[c], acc);
-    acc = df_add(acc, shfl_xor_df(acc, 1));
-    acc = df_add(acc, shfl_xor_df(acc, 2));
+  const int stage_elems = ncols * FRP + FR;
+  df64* st0 = reinterpret_cast<df64*>(smem_raw);
+  df64* hs = st0 + 2 * stage_elems;
+  __shared__ df64 red[8];
+  if (UPD)
+    for (int c = threadIdx.x; c < ncols; c += 256) hs[c] = h[c];
+  auto issue = [&](df64* st, int tile) {
+    const int64_t r0 = (int64_t)tile * FR;
+    for (int e = threadIdx.x; e < (ncols + 1) * (FR / 2); e += 256) {
+      const int c = e / (FR / 2), l = e - c * (FR / 2);
+      const int64_t row = r0 + 2 * l;
+      const bool ok = row < dim;
+      if (c < ncols)
+        cp_async16(st + c * FRP + 2 * l, ok ? (const void*)(Q + (int64_t)c * ldq + row) : (const void*)Q, ok);
+      else
+        cp_async16(st + ncols * FRP + 2 * l, ok ? (const void*)(w + row) : (const void*)w, ok);
+    }
+  };
+  df64 acc0 = df_zero(), acc1 = df_zero(), nrm = df_zero();
+  int stage = 0;
+  int tile = blockIdx.x;
+  if (tile < ntiles) issue(st0, tile);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    df64* cur = st0 + stage * stage_elems;
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles) issue(st0 + (stage ^ 1) * stage_elems, nxt);
+    cp_async_commit();
+    cp_async_wait<1>();
     __syncthreads();
-    if (q == 0) {
-      const df64 x = (r0 + r < dim) ? df_sub(ws[r], acc) : df_zero();
-      ws[r] = x;
-      if (r0 + r < dim) w[r0 + r] = x;
+    const df64* Qs = cur;
+    df64* ws = cur + ncols * FRP;
+    const int64_t r0 = (int64_t)tile * FR;
+    {  // rows of w (updated when UPD): 4 threads per row split the columns
+      const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+      df64 acc = df_zero();
+      if (UPD)
+        for (int c = q; c < ncols; c += 4) acc = df_fma(Qs[c * FRP + r], hs[c], acc);
+      acc = df_add(acc, shfl_xor_df(acc, 1));
+      acc = df_add(acc, shfl_xor_df(acc, 2));
+      __syncthreads();
+      if (q == 0) {
+        const df64 x = (r0 + r < dim) ? df_sub(ws[r], acc) : df_zero();
+        ws[r] = x;
+        if (UPD && r0 + r < dim) w[r0 + r] = x;
+        if (!PROJ) nrm = df_fma(x, x, nrm);
+      }
+    }
+    __syncthreads();
+    if (PROJ) {  // two threads per column (one per half tile); column ncols is w.w
+      const int half = threadIdx.x & 1;
+      const int c = threadIdx.x >> 1, c1 = (threadIdx.x + 256) >> 1;
+      if (c <= ncols) {
+        const df64* col = c < ncols ? Qs + c * FRP : ws;
+        for (int r = half * (FR / 2); r < (half + 1) * (FR / 2); ++r) acc0 = df_fma(col[r], ws[r], acc0);
+      }
+      if (c1 <= ncols) {
+        const df64* col = c1 < ncols ? Qs + c1 * FRP : ws;
+        for (int r = half * (FR / 2); r < (half + 1) * (FR / 2); ++r) acc1 = df_fma(col[r], ws[r], acc1);
+      }
+    }
+    __syncthreads();
+    stage ^= 1;
+  }
+  cp_async_wait<0>();
+  if (PROJ) {
+    acc0 = df_add(acc0, shfl_xor_df(acc0, 1));
+    acc1 = df_add(acc1, shfl_xor_df(acc1, 1));
+    const int c = threadIdx.x >> 1, c1 = (threadIdx.x + 256) >> 1;
+    if ((threadIdx.x & 1) == 0) {
+      if (c <= ncols) part[(int64_t)blockIdx.x * ldp + c] = acc0;
+      if (c1 <= ncols) part[(int64_t)blockIdx.x * ldp + c1] = acc1;
+    }
+  } else {
+    nrm = warp_sum_df(nrm);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      df64 t = df_zero();
+      for (int i = 0; i < 8; ++i) t = df_add(t, red[i]);
+      part[(int64_t)blockIdx.x * ldp + ncols] = t;
     }
   }
-  __syncthreads();
-  // projections of w' on every column (and w'.w'), two threads per column
-  // every thread runs the same number of iterations so the shuffle sees a full warp
-  const int tot = 2 * (ncols + 1);
-  for (int e0 = 0; e0 < tot; e0 += 256) {
-    const int e = e0 + threadIdx.x;
-    const int c = e >> 1, half = e & 1;
-    df64 acc = df_zero();
-    if (c <= ncols) {
-      const df64* col = c < ncols ? Qs + c * FRP : ws;
-      for (int r = half * (FR / 2); r < (half + 1) * (FR / 2); ++r) acc = df_fma(col[r], ws[r], acc);
-    }
-    acc = df_add(acc, shfl_xor_df(acc, 1));
-    if (half == 0 && c <= ncols) part[(int64_t)blockIdx.x * ldp + c] = acc;
-  }
+}
+
+// out[0] = sum_b part[b][col] (one value), for the norm column
+__global__ void k_reduce_one(const df64* __restrict__ part, int nblk, int ldp, int col, df64* __restrict__ out,
+                             const int* flag) {
+  if (flag && *flag == 0) return;
+  df64 s = df_zero();
+  for (int b = threadIdx.x; b < nblk; b += 32) s = df_add(s, part[(int64_t)b * ldp + col]);
+  s = warp_sum_df(s);
+  if (threadIdx.x == 0) *out = s;
 }
 
 // P3: w -= Q h; part[tile] = w.w over the tile; the last block sums the
@@ -803,6 +867,7 @@ static int grid_for(int64_t n, int threads, int cap) {
 
 int reorth_blocks(int64_t dim) { return (int)((dim + SLAB - 1) / SLAB); }
 int fused_tiles(int64_t dim) { return (int)((dim + FR - 1) / FR); }
+int fused_grid(size_t smem_bytes);
 
 // CGS2: w <- (I - Q Q^T)^2 w, nrm2 <- ||w||^2.  flag (may be null) gates the
 // whole sequence on the device (used for the breakdown replacement).
@@ -813,42 +878,70 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
   const double qb = 8.0 * (double)dim * ncols;
   const double fl = 2.0 * (double)dim * ncols;
   const int gated = flag ? 1 : 0;
-  if (ncols > 0) {
-    prof_begin(s);
-    k_cgs_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, flag);
-    prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
-    prof_begin(s);
-    k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part, G, rw.ldp, ncols, rw.h, flag);
-    prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
-    const int T2 = (int)((dim + FR - 1) / FR);
-    if (ncols <= FUSED_MAXCOL) {
-      const size_t sm = ((size_t)ncols * FRP + FR + ncols) * sizeof(df64);
+  if (ncols <= FUSED_MAXCOL) {
+    const int T2 = fused_tiles(dim);
+    const size_t sm = ((size_t)2 * (ncols * FRP + FR) + ncols) * sizeof(df64);
+    const int G2 = T2 < fused_grid(sm) ? T2 : fused_grid(sm);
+    const int ldp = rw.ldp2;
+    if (ncols > 0) {
       prof_begin(s);
-      k_cgs_update_proj<<<T2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, rw.ldp2, flag);
-      prof_end(s, gated ? K_GATED : K_UPDATE_PROJ, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : 2 * fl);
-      prof_begin(s);
-      k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part2, T2, rw.ldp2, ncols, rw.h, flag);
-      prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
-    } else {
-      prof_begin(s);
-      k_cgs_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
-      prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
-      prof_begin(s);
-      k_cgs_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, flag);
+      k_cgs_tiles<false, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag);
       prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
       prof_begin(s);
-      k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part, G, rw.ldp, ncols, rw.h, flag);
+      k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols, rw.h, flag);
+      prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+      prof_begin(s);
+      k_cgs_tiles<true, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag);
+      prof_end(s, gated ? K_GATED : K_UPDATE_PROJ, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : 2 * fl);
+      prof_begin(s);
+      k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols, rw.h, flag);
       prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
     }
+    prof_begin(s);
+    k_cgs_tiles<true, false><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag);
+    prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
+    prof_begin(s);
+    k_reduce_one<<<1, 32, 0, s>>>(rw.part2, G2, ldp, ncols, rw.nrm, flag);
+    prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+    return;
   }
+  // wide bases: batched passes (four reads of Q)
+  prof_begin(s);
+  k_cgs_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, flag);
+  prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
+  prof_begin(s);
+  k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part, G, rw.ldp, ncols, rw.h, flag);
+  prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+  prof_begin(s);
+  k_cgs_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
+  prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
+  prof_begin(s);
+  k_cgs_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, flag);
+  prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
+  prof_begin(s);
+  k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part, G, rw.ldp, ncols, rw.h, flag);
+  prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
   prof_begin(s);
   k_cgs_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
   prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
 }
 
+static int g_sms = 0;
 void reorth_setup() {
-  cudaFuncSetAttribute(k_cgs_update_proj, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(((size_t)FUSED_MAXCOL * FRP + FR + FUSED_MAXCOL) * sizeof(df64)));
+  const int mx = (int)(((size_t)2 * (FUSED_MAXCOL * FRP + FR) + FUSED_MAXCOL) * sizeof(df64));
+  cudaFuncSetAttribute(k_cgs_tiles<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_cgs_tiles<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_cgs_tiles<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+}
+// persistent grid of the fused pass: as many blocks as fit on every SM at once
+int fused_grid(size_t smem_bytes) {
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgs_tiles<true, true>, 256, smem_bytes);
+  if (per < 1) per = 1;
+  return (g_sms > 0 ? g_sms : 152) * per;
 }
 
 void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est, int* flag, int mode,
@@ -906,7 +999,7 @@ void launch_small_svd(const df64* B, int ldb, int r, int c, const int2* sched, S
     }
     prof_begin(s);
     k_svd_precondition<<<1, PRE_THREADS, pre_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, sched, cc, 40, 2e-6f);
-    prof_end(s, K_SMALL_SVD, 0.0, 0.0);
+    prof_end(s, K_SVD_PRE, 0.0, 0.0);
     warm = 1;
   }
   prof_begin(s);

@@ -18,6 +18,7 @@ enum KClass {
   K_UPDATE_PROJ,
   K_NORMALIZE,
   K_SMALL_SVD,
+  K_SVD_PRE,
   K_RITZ,
   K_HANKEL_SMALL,
   K_HANKEL_FS,
