@@ -176,6 +176,39 @@ int ssa_stats_get(ssa_kernel_stat_t* out, int max, int* count);
 /* Total kernels launched by the library in this process. */
 uint64_t ssa_kernel_launches(void);
 
+/* ---- allocation-free product (no counterpart in the paper) -------------- */
+
+/*
+ * ssa_matvec_noalloc -- y = X x (transpose = 0, x of length K, y of length L)
+ * or y = X^T x (transpose = 1, x of length L, y of length K) for the series
+ * f of length N, computing the spectrum of f and the product in one call
+ * without allocating any device memory.
+ *
+ * For callers that cannot allocate: code running under a host framework that
+ * owns all device memory through its own pool (a raw cudaMalloc there can
+ * fail or fragment the pool), and latency-critical paths where cudaMalloc /
+ * cudaFree, which may synchronise the device, are not acceptable.
+ *
+ * Its working memory (spectrum, FFT scratch, twiddle tables; about 1.3 MB)
+ * is one file-scope __device__ array of fixed size that every GPU which loads
+ * the library holds until the process exits.  Limits: N <= 65536; f, x and y
+ * must be device pointers (host buffers would need staging); precision is
+ * SSA_PREC_F64 or SSA_PREC_F32C.  Larger series or host buffers: use a plan
+ * (ssa_embed_plan, ssa_set_series, ssa_matvec).
+ *
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  Work is enqueued on `stream` (a cudaStream_t,
+ * NULL = default stream) and the call returns without synchronising.
+ * Every call reuses the same array: each call writes everything it reads
+ * (nothing needs to start at zero), so calls that overlap on the GPU -- on
+ * different streams, or from different threads -- race and must be ordered
+ * by the caller.
+ * Errors: SSA_EINVAL (NULL or host pointer, sizes, N > 65536), SSA_ECUDA.
+ */
+int ssa_matvec_noalloc(const double* f, int64_t N, int64_t L, int transpose, const double* x, double* y,
+                       int precision, void* stream);
+
 void ssa_plan_destroy(ssa_plan_t plan);
 void ssa_decomp_destroy(ssa_decomp_t d);
 const char* ssa_strerror(int code);

@@ -9,6 +9,7 @@ synthetic workloads.
 """
 from ._lib import (SSA_ENOCONV, SSA_OK, SSA_PREC_F32C, SSA_PREC_F64, SSAError, groups_csr, lib, make_opts,  # noqa: F401
                    ssa_decomp_destroy, ssa_decomp_get, ssa_decomp_info, ssa_decompose, ssa_default_opts,
-                   ssa_embed_plan, ssa_get_spectrum, ssa_hankelize, ssa_last_error, ssa_matvec, ssa_plan_destroy,
+                   ssa_embed_plan, ssa_get_spectrum, ssa_hankelize, ssa_last_error, ssa_matvec, ssa_matvec_noalloc,
+                   ssa_plan_destroy,
                    ssa_plan_info, ssa_reconstruct, ssa_set_series, ssa_stats_enable, ssa_stats_get,
                    ssa_kernel_launches, ssa_strerror)

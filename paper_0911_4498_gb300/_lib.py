@@ -54,6 +54,7 @@ _SIGS = {
     "ssa_hankelize": (_I, [_VP, _VP, _VP, _I64, _VP, _I64, _I, _VP, _VP, _I, _VP]),
     "ssa_plan_destroy": (None, [_VP]),
     "ssa_decomp_destroy": (None, [_VP]),
+    "ssa_matvec_noalloc": (_I, [_VP, _I64, _I64, _I, _VP, _VP, _I, _VP]),
     "ssa_stats_enable": (_I, [_I]),
     "ssa_stats_get": (_I, [ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "ssa_kernel_launches": (ctypes.c_uint64, []),
@@ -178,6 +179,10 @@ def ssa_plan_destroy(plan):
 
 def ssa_decomp_destroy(d):
     lib().ssa_decomp_destroy(d)
+
+
+def ssa_matvec_noalloc(f, N: int, L: int, transpose: int, x, y, precision=SSA_PREC_F64, stream=None):
+    _check(lib().ssa_matvec_noalloc(_ptr(f), N, L, int(transpose), _ptr(x), _ptr(y), precision, stream))
 
 
 def ssa_stats_enable(on: bool):

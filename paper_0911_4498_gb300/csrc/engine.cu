@@ -26,6 +26,10 @@ static void set_err(const char* fmt, ...) {
   vsnprintf(g_err, sizeof g_err, fmt, ap);
   va_end(ap);
 }
+namespace ssa {
+// detail message for ssa_last_error(), for the other translation units
+void host_set_error(const char* msg) { std::snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace ssa
 #define CK(x)                                                                   \
   do {                                                                          \
     cudaError_t e_ = (x);                                                       \
@@ -260,6 +264,8 @@ static std::vector<PendingLaunch> g_pending;
 static std::vector<cudaEvent_t> g_evpool;
 static ClassAcc g_acc[K_NCLASS];
 static thread_local cudaEvent_t g_begin = nullptr;
+static thread_local bool g_psup = false;
+void prof_suppress(bool on) { g_psup = on; }
 
 static cudaEvent_t ev_get() {
   if (!g_evpool.empty()) {
@@ -273,14 +279,14 @@ static cudaEvent_t ev_get() {
 }
 bool prof_enabled() { return g_pon; }
 void prof_begin(cudaStream_t s) {
-  if (!g_pon) return;
+  if (!g_pon || g_psup) return;
   std::lock_guard<std::mutex> lk(g_pmu);
   g_begin = ev_get();
   cudaEventRecord(g_begin, s);
 }
 void prof_end(cudaStream_t s, int cls, double bytes, double flops, int launches) {
   g_launches += launches;
-  if (!g_pon || !g_begin) return;
+  if (!g_pon || g_psup || !g_begin) return;
   std::lock_guard<std::mutex> lk(g_pmu);
   cudaEvent_t e = ev_get();
   cudaEventRecord(e, s);

@@ -31,5 +31,8 @@ void prof_begin(cudaStream_t s);
 void prof_end(cudaStream_t s, int cls, double bytes, double flops, int launches = 1);
 void prof_flush();
 bool prof_enabled();
+// while on (this thread), launches are counted but not timed (no host allocation)
+void prof_suppress(bool on);
+void host_set_error(const char* msg);
 
 }  // namespace ssa

@@ -18,7 +18,6 @@
 //   convolution identity of section 5 requires the quotient).
 #include <cstdio>
 #include <mutex>
-#include <unordered_map>
 #include "spectral.h"
 #include "fft.cuh"
 #include "prof.h"
@@ -382,16 +381,30 @@ constexpr int TH_COL = 256;
 constexpr int TH_ROW = 256;
 constexpr int MAXE_ROW = 4096;
 
-// Opt each kernel into the dynamic shared memory it needs, once per size.
+// Opt each kernel into the dynamic shared memory it needs, once per size
+// (fixed table, no heap allocation).
 template <class K> static void set_smem(K kern, size_t bytes) {
   static std::mutex mu;
-  static std::unordered_map<const void*, size_t> done;
+  static const void* keys[128];
+  static size_t vals[128];
+  static int used = 0;
   if (bytes <= 48 * 1024) return;
   std::lock_guard<std::mutex> lock(mu);
-  size_t& cur = done[reinterpret_cast<const void*>(kern)];
-  if (bytes > cur) {
+  const void* key = reinterpret_cast<const void*>(kern);
+  int i = 0;
+  while (i < used && keys[i] != key) ++i;
+  if (i == used) {
+    if (used == 128) {  // table full: set the attribute every time
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      return;
+    }
+    keys[used] = key;
+    vals[used] = 0;
+    ++used;
+  }
+  if (bytes > vals[i]) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cur = bytes;
+    vals[i] = bytes;
   }
 }
 
