@@ -11,8 +11,8 @@ is decompositions per second (each including its reconstruction).
   python bench.py --impl reference ...   # the CPU oracle on this host's cores
 
 Multi-GPU (torchrun, one rank per GPU) runs independent replicas: the path
-does not shard within one series, so each rank decomposes its
-own series and value = all ranks' decompositions / max rank time.
+does not shard within one series (a dependent chain of products), so each rank
+decomposes its own series and value = all ranks' decompositions / max rank time.
 """
 from __future__ import annotations
 
