@@ -137,6 +137,22 @@ def gpu_index_for_smi(local_rank):
     return local_rank
 
 
+def aggregate(elapsed_s, units, dist=None, device=None):
+    """Whole-job throughput over ranks: (sum of units) / (max rank time).
+
+    Each rank passes its own timed-region length and unit count; with a
+    process group the max time and the summed units are all-reduced.
+    """
+    if dist is None:
+        return units / elapsed_s, elapsed_s, units
+    import torch
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item()), float(u.item())
+
+
 # ----------------------------------------------------------------- CPU oracle sample
 def cpu_worker(args):
     """Run the oracle's Lanczos for a bounded number of half-steps (own process, 1 thread)."""
@@ -262,12 +278,10 @@ def run_gpu(args):
     stats = ssa.ssa_stats_get()
     ssa.ssa_stats_enable(False)
     clocks = sampler.stop()
+    value, elapsed_s, _ = aggregate(elapsed_ms / 1000.0, args.steps, dist, "cuda")
+    elapsed_ms = elapsed_s * 1000.0
     if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
         dist.barrier()
-    value = world * args.steps / (elapsed_ms / 1000.0)
 
     # accuracy against the oracle's stored values
     sig = sig_dev.cpu().numpy()
@@ -302,12 +316,42 @@ def run_gpu(args):
             step(f_pin, out_pin, sig_pin)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
-        if dist:
-            tt = torch.tensor([dt], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
-        e2e = {"value": world * n_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+        e2e_value, _, _ = aggregate(dt, n_e2e, dist, "cuda")
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * k + 8 * k * N}
+
+    # the other precision mode on the same workload (decomposition + reconstruction)
+    modes = None
+    if not args.no_modes:
+        other = ssa.SSA_PREC_F32C if prec == ssa.SSA_PREC_F64 else ssa.SSA_PREC_F64
+        plan2 = ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=other, seed=rank, stream=stream.cuda_stream))
+        sig2 = torch.empty(k, dtype=torch.float64, device="cuda")
+
+        def step2():
+            d, rc = ssa.ssa_decompose(plan2, f_dev, k)
+            try:
+                ssa.ssa_reconstruct(d, off_dev, idx_dev, k, out_dev)
+                ssa.ssa_decomp_get(d, sig2, None, None, None)
+            finally:
+                ssa.ssa_decomp_destroy(d)
+
+        for _ in range(max(1, args.warmup)):
+            step2()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step2()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v2, _, _ = aggregate(e0.elapsed_time(e1) / 1000.0, args.steps, dist, "cuda")
+        err2 = None
+        if gold is not None:
+            err2 = float(np.max(np.abs(sig2.cpu().numpy() - gold["sigma"][:k]) / gold["sigma"][:k]))
+        ssa.ssa_plan_destroy(plan2)
+        name_main = "f64" if prec == ssa.SSA_PREC_F64 else "f32c"
+        name_other = "f32c" if other == ssa.SSA_PREC_F32C else "f64"
+        modes = {name_main: {"value": value, "sigma_rel_err_max": sig_err},
+                 name_other: {"value": v2, "sigma_rel_err_max": err2}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -328,7 +372,7 @@ def run_gpu(args):
                 "sigma_rel_err_max": sig_err, "converged": bool(info.get("converged")),
                 "restarts": info.get("restarts"), "matvecs_per_decomp": info.get("matvecs"),
                 "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "modes": modes, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernels": per_kernel}
         print(json.dumps(line))
     if dist:
@@ -346,6 +390,7 @@ def main():
     ap.add_argument("--precision", default="f64", choices=["f64", "f32c"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--sample-halfsteps", type=int, default=6)
     ap.add_argument("--ref-halfsteps-full", type=int, default=400)
     ap.add_argument("--cpu-worker", action="store_true")

@@ -591,6 +591,7 @@ static int ensure_workspace(ssa_plan_t p, int d) {
   CK(cudaMalloc(&w.dummy, sizeof(df64)));
   CK(cudaMalloc(&w.flag, sizeof(int)));
   CK(cudaMalloc(&w.status, sizeof(unsigned)));
+  w.rw.status = w.status;
   CK(cudaMalloc(&w.sgn, cols * sizeof(int)));
   w.dcap = d;
   return SSA_OK;
@@ -704,6 +705,10 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     if (status & SSA_DEV_NONFINITE) {
       set_err("non-finite value in the Lanczos recurrence");
       return SSA_ENUMERIC;
+    }
+    if (status & SSA_DEV_TIMEOUT) {
+      set_err("a bounded device wait ran out in the reorthogonalisation");
+      return SSA_ETIMEOUT;
     }
     if (converged || restarts >= p->opts.max_restarts || kk >= cp) break;
     // thick restart: U <- U P[:, :kk], V <- [V Q[:, :kk], v_{c}], B <- [diag | rho]

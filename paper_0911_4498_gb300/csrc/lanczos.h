@@ -22,6 +22,7 @@ struct ReorthWork {
   df64* nrm;     // squared norm after the last update
   int* counter;  // last-block counter (returns to 0 after each kernel)
   df64* coop;    // [coop_blocks()][MAXCOL + 1] scratch of the breakdown branch
+  unsigned* status;  // device status word (SSA_DEV_* bits)
 };
 
 struct SvdWork {

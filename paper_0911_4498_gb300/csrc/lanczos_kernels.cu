@@ -142,32 +142,97 @@ SSA_D void cp_async16(void* smem, const void* gmem, bool valid) {
 SSA_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> SSA_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// ---- bulk copies (cp.async.bulk) completing on an mbarrier
+SSA_D unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+SSA_D void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+SSA_D void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+SSA_D void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+SSA_D bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+SSA_D void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+SSA_D void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// Bounded wait: gives up after ~2^26 polls (seconds), so a copy that never
+// lands becomes an error status instead of a hang.
+SSA_D bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 26); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ---- lazy double-float accumulation: value = hi + lo with lo unnormalised
+struct dacc {
+  float hi, lo;
+};
+SSA_D dacc dacc_zero() { return {0.f, 0.f}; }
+// s += a * b (12 FP32 instructions; renormalise with dacc_norm every few dozen terms)
+SSA_D void dacc_fma(dacc& s, df64 a, df64 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float t = s.hi + p;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  s.hi = t;
+  s.lo += err + e;
+}
+SSA_D df64 dacc_val(dacc s) { return fast_two_sum(s.hi, s.lo); }
+SSA_D void dacc_norm(dacc& s) {
+  const df64 v = fast_two_sum(s.hi, s.lo);
+  s.hi = v.hi;
+  s.lo = v.lo;
+}
+
 // Tile-walking CGS pass over Q (dim x ncols, ncols <= FUSED_MAXCOL):
 //   UPD:  w <- w - Q h          (h read from memory)
 //   PROJ: part[block][c] = sum over the block's tiles of Q[tile, c] . w[tile]
 //   always: part[block][ncols] = sum of w.w over the block's tiles (after UPD)
-// Persistent blocks walk tiles of FR rows; each tile (all ncols columns and the
-// w rows) is copied to shared memory asynchronously and double-buffered, so
-// many 16-byte copies are in flight per SM without holding registers.  The
-// projections accumulate per (column, half-tile) thread across tiles, so a
-// block writes one partial row.
-constexpr int FR = 64;
-constexpr int FRP = 66;  // column stride in shared memory (16-byte aligned, fewer bank conflicts)
+// Persistent blocks walk tiles of FR rows; every thread copies its share of
+// the next tile (all columns and the w rows) to shared memory with 16-byte
+// asynchronous copies while the current tile is processed (double buffer).
+// The compute threads read two rows at a time (128-bit shared loads) and
+// accumulate with a 12-instruction double-float multiply-add.  (One-thread
+// bulk copies of the 512-byte column segments measured slower: the copy
+// engine serialises many small requests.)
+constexpr int FR = 64;   // rows per tile
+constexpr int FRP = 66;  // column stride in shared memory (16-byte aligned)
+constexpr int NST = 2;   // pipeline stages (tiles in shared memory per block); 32-row tiles with
+                         // 4 stages measured slower (more per-tile overhead)
 template <bool UPD, bool PROJ>
 __global__ void __launch_bounds__(256) k_cgs_tiles(const df64* __restrict__ Q, int64_t ldq, int ncols,
                                                    df64* __restrict__ w, int64_t dim, const df64* __restrict__ h,
-                                                   df64* __restrict__ part, int ldp, int ntiles, const int* flag) {
+                                                   df64* __restrict__ part, int ldp, int ntiles, const int* flag,
+                                                   unsigned* status) {
   if (flag && *flag == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ df64 red[8];
   const int stage_elems = ncols * FRP + FR;
   df64* st0 = reinterpret_cast<df64*>(smem_raw);
-  df64* hs = st0 + 2 * stage_elems;
-  __shared__ df64 red[8];
+  df64* hs = st0 + NST * stage_elems;
+  const int tid = threadIdx.x;
   if (UPD)
-    for (int c = threadIdx.x; c < ncols; c += 256) hs[c] = h[c];
-  auto issue = [&](df64* st, int tile) {
+    for (int c = tid; c < ncols; c += 256) hs[c] = h[c];
+  auto issue = [&](int stg, int tile) {  // all threads: 16-byte asynchronous copies
     const int64_t r0 = (int64_t)tile * FR;
-    for (int e = threadIdx.x; e < (ncols + 1) * (FR / 2); e += 256) {
+    df64* st = st0 + stg * stage_elems;
+    for (int e = tid; e < (ncols + 1) * (FR / 2); e += 256) {
       const int c = e / (FR / 2), l = e - c * (FR / 2);
       const int64_t row = r0 + 2 * l;
       const bool ok = row < dim;
@@ -177,66 +242,102 @@ __global__ void __launch_bounds__(256) k_cgs_tiles(const df64* __restrict__ Q, i
         cp_async16(st + ncols * FRP + 2 * l, ok ? (const void*)(w + row) : (const void*)w, ok);
     }
   };
-  df64 acc0 = df_zero(), acc1 = df_zero(), nrm = df_zero();
-  int stage = 0;
-  int tile = blockIdx.x;
-  if (tile < ntiles) issue(st0, tile);
-  cp_async_commit();
-  for (; tile < ntiles; tile += gridDim.x) {
-    df64* cur = st0 + stage * stage_elems;
-    const int nxt = tile + gridDim.x;
-    if (nxt < ntiles) issue(st0 + (stage ^ 1) * stage_elems, nxt);
+  dacc acc0 = dacc_zero(), acc1 = dacc_zero();
+  df64 nrm = df_zero();
+  // prologue: the first NST-1 tiles of this block in flight
+  for (int p = 0; p < NST - 1; ++p) {
+    const int t = blockIdx.x + p * gridDim.x;
+    if (t < ntiles) issue(p, t);
     cp_async_commit();
-    cp_async_wait<1>();
+  }
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int stage = it % NST;
+    const int ahead = tile + (NST - 1) * gridDim.x;
+    if (ahead < ntiles) issue((it + NST - 1) % NST, ahead);
+    cp_async_commit();
+    cp_async_wait<NST - 1>();
     __syncthreads();
-    const df64* Qs = cur;
-    df64* ws = cur + ncols * FRP;
+    const df64* Qs = st0 + stage * stage_elems;
+    df64* ws = const_cast<df64*>(Qs) + ncols * FRP;
     const int64_t r0 = (int64_t)tile * FR;
-    {  // rows of w (updated when UPD): 4 threads per row split the columns
-      const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
-      df64 acc = df_zero();
-      if (UPD)
-        for (int c = q; c < ncols; c += 4) acc = df_fma(Qs[c * FRP + r], hs[c], acc);
-      acc = df_add(acc, shfl_xor_df(acc, 1));
-      acc = df_add(acc, shfl_xor_df(acc, 2));
+    {  // rows 2rp, 2rp+1 of w (updated when UPD); 8 threads per row pair split the columns
+      const int rp = tid >> 3, q = tid & 7;
+      dacc a0 = dacc_zero(), a1 = dacc_zero();
+      if (UPD) {
+        for (int c = q; c < ncols; c += 8) {
+          const float4 v = *reinterpret_cast<const float4*>(Qs + c * FRP + 2 * rp);
+          const df64 hc = hs[c];
+          dacc_fma(a0, make_df(v.x, v.y), hc);
+          dacc_fma(a1, make_df(v.z, v.w), hc);
+        }
+      }
+      df64 s0 = dacc_val(a0), s1 = dacc_val(a1);
+#pragma unroll
+      for (int m = 1; m < 8; m <<= 1) {
+        s0 = df_add(s0, shfl_xor_df(s0, m));
+        s1 = df_add(s1, shfl_xor_df(s1, m));
+      }
       __syncthreads();
       if (q == 0) {
-        const df64 x = (r0 + r < dim) ? df_sub(ws[r], acc) : df_zero();
-        ws[r] = x;
-        if (UPD && r0 + r < dim) w[r0 + r] = x;
-        if (!PROJ) nrm = df_fma(x, x, nrm);
+        const int64_t g0 = r0 + 2 * rp;
+        const df64 x0 = g0 < dim ? df_sub(ws[2 * rp], s0) : df_zero();
+        const df64 x1 = g0 + 1 < dim ? df_sub(ws[2 * rp + 1], s1) : df_zero();
+        ws[2 * rp] = x0;
+        ws[2 * rp + 1] = x1;
+        if (UPD) {
+          if (g0 < dim) w[g0] = x0;
+          if (g0 + 1 < dim) w[g0 + 1] = x1;
+        }
+        if (!PROJ) {
+          nrm = df_fma(x0, x0, nrm);
+          nrm = df_fma(x1, x1, nrm);
+        }
       }
     }
     __syncthreads();
     if (PROJ) {  // two threads per column (one per half tile); column ncols is w.w
-      const int half = threadIdx.x & 1;
-      const int c = threadIdx.x >> 1, c1 = (threadIdx.x + 256) >> 1;
+      const int half = tid & 1;
+      const int c = tid >> 1, c1 = (tid + 256) >> 1;
+      const float4* wv = reinterpret_cast<const float4*>(ws + half * (FR / 2));
       if (c <= ncols) {
-        const df64* col = c < ncols ? Qs + c * FRP : ws;
-        for (int r = half * (FR / 2); r < (half + 1) * (FR / 2); ++r) acc0 = df_fma(col[r], ws[r], acc0);
+        const float4* col = reinterpret_cast<const float4*>((c < ncols ? Qs + c * FRP : ws) + half * (FR / 2));
+#pragma unroll 4
+        for (int i = 0; i < FR / 4; ++i) {
+          const float4 qv = col[i], xv = wv[i];
+          dacc_fma(acc0, make_df(qv.x, qv.y), make_df(xv.x, xv.y));
+          dacc_fma(acc0, make_df(qv.z, qv.w), make_df(xv.z, xv.w));
+        }
+        dacc_norm(acc0);
       }
       if (c1 <= ncols) {
-        const df64* col = c1 < ncols ? Qs + c1 * FRP : ws;
-        for (int r = half * (FR / 2); r < (half + 1) * (FR / 2); ++r) acc1 = df_fma(col[r], ws[r], acc1);
+        const float4* col = reinterpret_cast<const float4*>((c1 < ncols ? Qs + c1 * FRP : ws) + half * (FR / 2));
+#pragma unroll 4
+        for (int i = 0; i < FR / 4; ++i) {
+          const float4 qv = col[i], xv = wv[i];
+          dacc_fma(acc1, make_df(qv.x, qv.y), make_df(xv.x, xv.y));
+          dacc_fma(acc1, make_df(qv.z, qv.w), make_df(xv.z, xv.w));
+        }
+        dacc_norm(acc1);
       }
     }
     __syncthreads();
-    stage ^= 1;
   }
   cp_async_wait<0>();
   if (PROJ) {
-    acc0 = df_add(acc0, shfl_xor_df(acc0, 1));
-    acc1 = df_add(acc1, shfl_xor_df(acc1, 1));
-    const int c = threadIdx.x >> 1, c1 = (threadIdx.x + 256) >> 1;
-    if ((threadIdx.x & 1) == 0) {
-      if (c <= ncols) part[(int64_t)blockIdx.x * ldp + c] = acc0;
-      if (c1 <= ncols) part[(int64_t)blockIdx.x * ldp + c1] = acc1;
+    df64 v0 = dacc_val(acc0), v1 = dacc_val(acc1);
+    v0 = df_add(v0, shfl_xor_df(v0, 1));
+    v1 = df_add(v1, shfl_xor_df(v1, 1));
+    const int c = tid >> 1, c1 = (tid + 256) >> 1;
+    if ((tid & 1) == 0) {
+      if (c <= ncols) part[(int64_t)blockIdx.x * ldp + c] = v0;
+      if (c1 <= ncols) part[(int64_t)blockIdx.x * ldp + c1] = v1;
     }
   } else {
     nrm = warp_sum_df(nrm);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    if ((tid & 31) == 0) red[tid >> 5] = nrm;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       df64 t = df_zero();
       for (int i = 0; i < 8; ++i) t = df_add(t, red[i]);
       part[(int64_t)blockIdx.x * ldp + ncols] = t;
@@ -880,25 +981,25 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
   const int gated = flag ? 1 : 0;
   if (ncols <= FUSED_MAXCOL) {
     const int T2 = fused_tiles(dim);
-    const size_t sm = ((size_t)2 * (ncols * FRP + FR) + ncols) * sizeof(df64);
+    const size_t sm = ((size_t)NST * (ncols * FRP + FR) + ncols) * sizeof(df64);
     const int G2 = T2 < fused_grid(sm) ? T2 : fused_grid(sm);
     const int ldp = rw.ldp2;
     if (ncols > 0) {
       prof_begin(s);
-      k_cgs_tiles<false, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag);
+      k_cgs_tiles<false, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag, rw.status);
       prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
       prof_begin(s);
       k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols, rw.h, flag);
       prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
       prof_begin(s);
-      k_cgs_tiles<true, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag);
+      k_cgs_tiles<true, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag, rw.status);
       prof_end(s, gated ? K_GATED : K_UPDATE_PROJ, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : 2 * fl);
       prof_begin(s);
       k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols, rw.h, flag);
       prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
     }
     prof_begin(s);
-    k_cgs_tiles<true, false><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag);
+    k_cgs_tiles<true, false><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag, rw.status);
     prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
     prof_begin(s);
     k_reduce_one<<<1, 32, 0, s>>>(rw.part2, G2, ldp, ncols, rw.nrm, flag);
@@ -928,7 +1029,7 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
 
 static int g_sms = 0;
 void reorth_setup() {
-  const int mx = (int)(((size_t)2 * (FUSED_MAXCOL * FRP + FR) + FUSED_MAXCOL) * sizeof(df64));
+  const int mx = (int)(((size_t)NST * (FUSED_MAXCOL * FRP + FR) + FUSED_MAXCOL) * sizeof(df64));
   cudaFuncSetAttribute(k_cgs_tiles<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_cgs_tiles<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_cgs_tiles<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
