@@ -70,9 +70,16 @@ typedef struct ssa_opts {
   int keep;           /* Ritz pairs kept per restart (0 = k + ceil((d-k)/2)) */
   uint64_t seed;      /* splitmix64 seed of the starting vector p_0 and breakdown vectors */
   void* stream;       /* cudaStream_t for all GPU work (NULL = default stream) */
+  int refine;         /* SSA_REFINE_ON: return each sigma_i as the Rayleigh quotient u_i^T X v_i of the
+                         returned vectors, computed with native-FP64 FFT products (k extra products);
+                         SSA_REFINE_OFF (default): return the Ritz values of the projected matrix */
 } ssa_opts_t;
 
-/* Fill *opts with defaults: SSA_PREC_F64, tol 0 (precision default), 200 restarts, seed 0, NULL stream. */
+#define SSA_REFINE_OFF 0
+#define SSA_REFINE_ON 1
+
+/* Fill *opts with defaults: SSA_PREC_F64, tol 0 (precision default), 200 restarts, seed 0, NULL stream,
+ * SSA_REFINE_OFF. */
 void ssa_default_opts(ssa_opts_t* opts);
 
 /*
@@ -150,6 +157,36 @@ int ssa_reconstruct(ssa_decomp_t d, const int32_t* grp_off, const int32_t* grp_i
  */
 int ssa_hankelize(ssa_plan_t plan, const double* sigma, const double* U, int64_t ldu, const double* V, int64_t ldv,
                   int r, const int32_t* grp_off, const int32_t* grp_idx, int m, double* out);
+
+/* ---- batched decompositions (many series in one launch) ----------------- */
+
+typedef struct ssa_batch_s* ssa_batch_t;
+
+/*
+ * The truncated SVD of ssa_decompose for nseries independent series in one
+ * persistent launch: each CTA of the GPU takes series from a device work
+ * queue (largest first) and runs the whole method for that series inside
+ * the CTA (spectrum, Algorithms 1-3 with CGS2 reorthogonalisation, thick
+ * restart, projected SVD, Ritz vectors, sign rule).
+ *   f:        all series back to back (host or device), series i is
+ *             f[offsets[i] .. offsets[i+1]-1], offsets[0] = 0 (nseries + 1 int64)
+ *   Ls, ks:   window and number of triples per series (nseries each)
+ *   opts:     as for plans; opts->krylov_dim / keep apply to every series.
+ * Limits: N <= 32768 (SSA_PREC_F32C) or N <= 16384 (SSA_PREC_F64); Krylov
+ * dimension min(max(2k, k+32), min(L, K)) <= 72, so k <= 40.
+ * On SSA_OK or SSA_ENOCONV (some series not converged) *out holds the results.
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ENOCONV, SSA_ENUMERIC, SSA_ECUDA.
+ */
+int ssa_decompose_batch(int nseries, const double* f, const int64_t* offsets, const int64_t* Ls, const int32_t* ks,
+                        const ssa_opts_t* opts, ssa_batch_t* out);
+
+/* Facts of series i: k, converged flag, thick restarts, products applied. */
+int ssa_batch_info(ssa_batch_t b, int i, int* k, int* converged, int* restarts, int64_t* matvecs);
+
+/* Results of series i: sigma (k), U (L x k), V (K x k), resid (k); NULL skips an output. */
+int ssa_batch_get(ssa_batch_t b, int i, double* sigma, double* U, double* V, double* resid);
+
+void ssa_batch_destroy(ssa_batch_t b);
 
 /* ---- launch accounting (not part of the paper's method) ---------------- */
 

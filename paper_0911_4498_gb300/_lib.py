@@ -18,12 +18,13 @@ LIB_PATH = os.path.join(HERE, "libssa_gb300.so")
 
 SSA_OK, SSA_EINVAL, SSA_ENOMEM, SSA_ENOCONV, SSA_ETIMEOUT, SSA_ECUDA, SSA_ENUMERIC = range(7)
 SSA_PREC_F64, SSA_PREC_F32C = 0, 1
+SSA_REFINE_OFF, SSA_REFINE_ON = 0, 1
 
 
 class SsaOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
                 ("krylov_dim", ctypes.c_int), ("keep", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("refine", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -55,6 +56,11 @@ _SIGS = {
     "ssa_plan_destroy": (None, [_VP]),
     "ssa_decomp_destroy": (None, [_VP]),
     "ssa_matvec_noalloc": (_I, [_VP, _I64, _I64, _I, _VP, _VP, _I, _VP]),
+    "ssa_decompose_batch": (_I, [_I, _VP, _VP, _VP, _VP, ctypes.POINTER(SsaOpts), ctypes.POINTER(_VP)]),
+    "ssa_batch_info": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                            ctypes.POINTER(_I64)]),
+    "ssa_batch_get": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "ssa_batch_destroy": (None, [_VP]),
     "ssa_stats_enable": (_I, [_I]),
     "ssa_stats_get": (_I, [ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "ssa_kernel_launches": (ctypes.c_uint64, []),
@@ -99,7 +105,7 @@ def _ptr(x, dtype=np.float64):
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
         import torch
-        want = torch.float64 if dtype == np.float64 else torch.int32
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}[dtype]
         if x.dtype != want or not x.is_contiguous():
             raise TypeError(f"need a contiguous {want} tensor")
         return x.data_ptr()
@@ -112,11 +118,13 @@ def ssa_default_opts() -> SsaOpts:
     return o
 
 
-def make_opts(precision=SSA_PREC_F64, tol=0.0, max_restarts=200, krylov_dim=0, keep=0, seed=0, stream=None):
+def make_opts(precision=SSA_PREC_F64, tol=0.0, max_restarts=200, krylov_dim=0, keep=0, seed=0, stream=None,
+              refine=SSA_REFINE_OFF):
     o = ssa_default_opts()
     o.precision, o.tol, o.max_restarts = precision, tol, max_restarts
     o.krylov_dim, o.keep, o.seed = krylov_dim, keep, seed
     o.stream = stream
+    o.refine = refine
     return o
 
 
@@ -183,6 +191,31 @@ def ssa_decomp_destroy(d):
 
 def ssa_matvec_noalloc(f, N: int, L: int, transpose: int, x, y, precision=SSA_PREC_F64, stream=None):
     _check(lib().ssa_matvec_noalloc(_ptr(f), N, L, int(transpose), _ptr(x), _ptr(y), precision, stream))
+
+
+def ssa_decompose_batch(f, offsets, Ls, ks, opts: SsaOpts | None = None):
+    """Returns (batch handle, status); status is SSA_OK or SSA_ENOCONV."""
+    h = _VP()
+    n = len(Ls)
+    rc = _check(lib().ssa_decompose_batch(n, _ptr(f), _ptr(offsets, np.int64), _ptr(Ls, np.int64),
+                                          _ptr(ks, np.int32), ctypes.byref(opts) if opts is not None else None,
+                                          ctypes.byref(h)), allow=(SSA_ENOCONV,))
+    return h, rc
+
+
+def ssa_batch_info(b, i: int):
+    k, conv, rs = _I(), _I(), _I()
+    mv = _I64()
+    _check(lib().ssa_batch_info(b, i, ctypes.byref(k), ctypes.byref(conv), ctypes.byref(rs), ctypes.byref(mv)))
+    return {"k": k.value, "converged": bool(conv.value), "restarts": rs.value, "matvecs": mv.value}
+
+
+def ssa_batch_get(b, i: int, sigma=None, U=None, V=None, resid=None):
+    _check(lib().ssa_batch_get(b, i, _ptr(sigma), _ptr(U), _ptr(V), _ptr(resid)))
+
+
+def ssa_batch_destroy(b):
+    lib().ssa_batch_destroy(b)
 
 
 def ssa_stats_enable(on: bool):

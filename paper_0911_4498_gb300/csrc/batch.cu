@@ -1,0 +1,1042 @@
+// Batched decompositions: many independent series of uneven length in one
+// persistent launch.  Each CTA takes series from a device work queue (largest
+// first) and runs the whole method for one series at a time, in the CTA:
+//   spectrum of the series (Algorithm 2 steps 1-2, double-float),
+//   Golub-Kahan-Lanczos bidiagonalisation (Algorithm 1) with every product by
+//   Algorithms 2/3 as a single-CTA FFT in shared memory, CGS2
+//   reorthogonalisation (section 3.2.2) streaming the basis through shared
+//   memory, thick restart (section 3.3) with the one-CTA Jacobi SVD of the
+//   projected matrix, Ritz vectors and the sign rule.
+// Per-CTA scratch (bases, projected matrix, SVD work, spectrum) lives in one
+// slot of a pool sized for the largest series of the batch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "ssa.h"
+#include "fft.cuh"
+#include "lanczos_dev.cuh"
+#include "prof.h"
+#include "spectral.h"
+
+namespace ssa {
+
+constexpr int BT = 512;                 // threads per CTA
+constexpr int B_SMEM = 128 * 1024;      // dynamic shared memory (FFT buffer, reused by every phase)
+constexpr int B_MAXD = 72;              // largest Krylov dimension of a batched series
+constexpr int B_MAXC = B_MAXD + 2;      // basis columns / projected-matrix size
+constexpr int B_FR = 64;                // CGS tile rows
+constexpr int B_FRP = 66;               // CGS tile column stride
+
+struct BSeries {
+  int64_t f_off, N, L, K;  // user sizes
+  int64_t Lw, Kw;          // working orientation (Lw <= Kw)
+  int transposed;
+  int k, d, kk;
+  int lg_n;                // n = M / 2
+  int64_t out_u, out_v, out_s;
+};
+
+struct BCtx {
+  const BSeries* ser;
+  int nseries;
+  const int* order;
+  int* next;
+  const double* f;
+  double *out_U, *out_V, *out_sigma, *out_resid;
+  int* out_info;  // per series: converged, restarts, matvecs, status
+  const cplx<df64>* tw;
+  int lg_P;
+  const cplx<df64>* tA;
+  const cplx<df64>* tB;
+  int tws;
+  int lg_Mmax;
+  char* slots;
+  int64_t slot_bytes;
+  int64_t ldu, ldv;  // basis leading dimensions of a slot
+  int nmax;          // largest n of the batch
+  int precision;
+  double tol;
+  int max_restarts;
+  uint64_t seed;
+};
+
+struct Slot {  // carved out of the CTA's slot
+  df64 *U[2], *V[2], *B, *A, *W, *P, *Q, *T, *sigma, *y;
+  cplx<df64>* chat;
+  cplx<df64>* fscr;
+  double *resid, *sigma_d;
+};
+
+SSA_D Slot carve(const BCtx& cx, int slot_id) {
+  char* base = cx.slots + (int64_t)slot_id * cx.slot_bytes;
+  Slot s;
+  df64* p = reinterpret_cast<df64*>(base);
+  for (int i = 0; i < 2; ++i) { s.U[i] = p; p += cx.ldu * B_MAXC; }
+  for (int i = 0; i < 2; ++i) { s.V[i] = p; p += cx.ldv * B_MAXC; }
+  s.B = p; p += B_MAXC * B_MAXC;
+  s.A = p; p += B_MAXC * B_MAXC;
+  s.W = p; p += B_MAXC * B_MAXC;
+  s.P = p; p += B_MAXC * B_MAXC;
+  s.Q = p; p += B_MAXC * B_MAXC;
+  s.T = p; p += B_MAXC * B_MAXC;
+  s.sigma = p; p += B_MAXC + 2;
+  s.y = p; p += cx.ldv;
+  s.chat = reinterpret_cast<cplx<df64>*>(p);
+  s.fscr = s.chat + (cx.nmax + 2);
+  double* d = reinterpret_cast<double*>(s.fscr + cx.nmax);
+  s.resid = d;
+  s.sigma_d = d + B_MAXC + 2;
+  return s;
+}
+
+int64_t slot_bytes_for(int64_t ldu, int64_t ldv, int nmax) {
+  int64_t dfs = 2 * ldu * B_MAXC + 2 * ldv * B_MAXC + 6 * B_MAXC * B_MAXC + (B_MAXC + 2) + ldv;
+  int64_t bytes = dfs * 8 + (int64_t)(2 * nmax + 2) * 16 + 2 * (B_MAXC + 2) * 8;
+  return (bytes + 255) / 256 * 256;
+}
+
+// ---------------------------------------------------------------- spectrum
+// c-hat = rFFT_M(c) in df64, scaled by 1/(4n), natural order.  n <= 8192 in
+// shared memory; n = 16384 as two half-length FFTs (even / odd packed
+// samples) combined through global scratch.
+SSA_D double circ(const Geom& g, const double* f, int64_t j) {
+  if (j < g.L) return f[g.N - g.L + j];
+  const int64_t j0 = g.L + (g.M - g.N);
+  return j >= j0 ? f[j - j0] : 0.0;
+}
+
+SSA_D void cta_spectrum(const Geom& g, const double* f, cplx<df64>* chat, cplx<df64>* scr, cplx<df64>* buf) {
+  const int n = 1 << g.lg_n;
+  const float s = 0.5f / (4.0f * (float)n);
+  const cplx<df64>* Z;
+  if (n <= 8192) {
+    for (int t = threadIdx.x; t < n; t += BT)
+      buf[t] = mk(df_from_double(circ(g, f, 2 * (int64_t)t)), df_from_double(circ(g, f, 2 * (int64_t)t + 1)));
+    __syncthreads();
+    cta_fft<df64, BT, 8192, false>(buf, g.lg_n, 1, g.tw, g.lg_P);
+    Z = buf;
+  } else {
+    const int h = n / 2;
+    for (int par = 0; par < 2; ++par) {
+      for (int t = threadIdx.x; t < h; t += BT) {
+        const int64_t j = 4 * (int64_t)t + 2 * par;  // z[2t + par] = c[2(2t+par)] + i c[2(2t+par)+1]
+        buf[t] = mk(df_from_double(circ(g, f, j)), df_from_double(circ(g, f, j + 1)));
+      }
+      __syncthreads();
+      cta_fft<df64, BT, 8192, false>(buf, g.lg_n - 1, 1, g.tw, g.lg_P);
+      if (par == 0) {
+        for (int t = threadIdx.x; t < h; t += BT) scr[t] = buf[t];
+        __syncthreads();
+      }
+    }
+    for (int k = threadIdx.x; k < h; k += BT) {  // Z[k] = E[k] + W_n^k O[k], Z[k+h] = E[k] - W_n^k O[k]
+      const cplx<df64> e = scr[k];
+      const cplx<df64> t = c_mul(buf[k], tw_load<df64>(g.tw, (int64_t)k << (g.lg_P - g.lg_n)));
+      scr[k] = c_add(e, t);
+      scr[k + h] = c_sub(e, t);
+    }
+    __syncthreads();
+    Z = scr;
+  }
+  for (int k = threadIdx.x; k <= n / 2; k += BT) {
+    const int nk = (n - k) & (n - 1);
+    const cplx<df64> tw = k ? twiddle_M<df64>(g.tA, g.tB, g.tws, (int64_t)k << g.twshift)
+                            : mk(make_df(1.f, 0.f), df_zero());
+    cplx<df64> wk, wnk;
+    rfft_post(Z[k], Z[nk], tw, wk, wnk);
+    chat[k] = c_scale(wk, s);
+    chat[n - k] = c_scale(wnk, s);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- products
+template <class T> SSA_D T ldx(const df64* p, int64_t i) { return scal<T>::from_df(p[i]); }
+
+// y = X x (transpose = 0) or X^T x (transpose = 1), one CTA, FFT in shared memory.
+template <class T, int MAXE>
+SSA_D void cta_matvec(const Geom& g, int transpose, const df64* x, df64* y, const cplx<df64>* chat, cplx<T>* buf) {
+  const int n = 1 << g.lg_n;
+  for (int t = threadIdx.x; t < n; t += BT) {
+    T v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int64_t j = 2 * (int64_t)t + e;
+      if (!transpose) v[e] = j < g.K ? ldx<T>(x, g.K - 1 - j) : scal<T>::zero();
+      else v[e] = j >= g.M - g.L ? ldx<T>(x, g.M - 1 - j) : scal<T>::zero();
+    }
+    buf[t] = mk(v[0], v[1]);
+  }
+  __syncthreads();
+  cta_fft<T, BT, MAXE, false>(buf, g.lg_n, 1, g.tw, g.lg_P);
+  for (int k = threadIdx.x; k <= n / 2; k += BT) {
+    const int nk = (n - k) & (n - 1);
+    cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)k << g.twshift)
+                   : mk(scal<T>::from_double(1.0), scal<T>::zero());
+    cplx<T> wk, wnk, zk, znk;
+    rfft_post(buf[k], buf[nk], tw, wk, wnk);
+    cplx<T> pk = mul_spec(wk, chat[k]);
+    cplx<T> pnk = mul_spec(wnk, chat[n - k]);
+    irfft_pre(pk, pnk, tw, zk, znk);
+    buf[k] = zk;
+    if (k != 0 && nk != k) buf[nk] = znk;
+  }
+  __syncthreads();
+  cta_fft<T, BT, MAXE, true>(buf, g.lg_n, 1, g.tw, g.lg_P);
+  const int64_t off = transpose ? g.M - g.K : 0;
+  const int64_t cnt = transpose ? g.K : g.L;
+  for (int64_t m = threadIdx.x; m < cnt; m += BT) {
+    const int64_t i = off + m;
+    const cplx<T> z = buf[i >> 1];
+    y[m] = scal<T>::to_df((i & 1) ? z.im : z.re);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- CGS2 in one CTA
+// One pass over the basis Q (dim x ncols) in tiles of B_FR rows, double
+// buffered in shared memory by 16-byte asynchronous copies:
+//   UPD:  w <- w - Q h_in;   PROJ: h_out[c] = Q[:, c] . w (c < ncols), h_out[ncols] = w.w
+//   !PROJ: *nrm_out = w.w
+template <bool UPD, bool PROJ>
+SSA_D void cta_cgs_pass(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, const df64* h_in, df64* h_out,
+                        df64* nrm_out, df64* stbuf) {
+  const int tid = threadIdx.x;
+  const int stage_elems = ncols * B_FRP + B_FR;
+  const int ntiles = (int)((dim + B_FR - 1) / B_FR);
+  auto issue = [&](int stg, int tile) {
+    const int64_t r0 = (int64_t)tile * B_FR;
+    df64* st = stbuf + stg * stage_elems;
+    for (int e = tid; e < (ncols + 1) * (B_FR / 2); e += BT) {
+      const int c = e / (B_FR / 2), l = e - c * (B_FR / 2);
+      const int64_t row = r0 + 2 * l;
+      const bool ok = row < dim;
+      if (c < ncols)
+        cp_async16(st + c * B_FRP + 2 * l, ok ? (const void*)(Q + (int64_t)c * ldq + row) : (const void*)Q, ok);
+      else
+        cp_async16(st + ncols * B_FRP + 2 * l, ok ? (const void*)(w + row) : (const void*)w, ok);
+    }
+  };
+  dacc acc = dacc_zero();
+  df64 nrm = df_zero();
+  issue(0, 0);
+  cp_async_commit();
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int stage = tile & 1;
+    if (tile + 1 < ntiles) issue(stage ^ 1, tile + 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const df64* Qs = stbuf + stage * stage_elems;
+    df64* ws = const_cast<df64*>(Qs) + ncols * B_FRP;
+    const int64_t r0 = (int64_t)tile * B_FR;
+    {  // 32 row pairs x 16 threads per pair
+      const int rp = tid >> 4, q = tid & 15;
+      dacc a0 = dacc_zero(), a1 = dacc_zero();
+      if (UPD) {
+        for (int c = q; c < ncols; c += 16) {
+          const float4 v = *reinterpret_cast<const float4*>(Qs + c * B_FRP + 2 * rp);
+          const df64 hc = h_in[c];
+          dacc_fma(a0, make_df(v.x, v.y), hc);
+          dacc_fma(a1, make_df(v.z, v.w), hc);
+        }
+      }
+      df64 s0 = dacc_val(a0), s1 = dacc_val(a1);
+#pragma unroll
+      for (int m = 1; m < 16; m <<= 1) {
+        s0 = df_add(s0, shfl_xor_df(s0, m));
+        s1 = df_add(s1, shfl_xor_df(s1, m));
+      }
+      __syncthreads();
+      if (q == 0) {
+        const int64_t g0 = r0 + 2 * rp;
+        const df64 x0 = g0 < dim ? df_sub(ws[2 * rp], s0) : df_zero();
+        const df64 x1 = g0 + 1 < dim ? df_sub(ws[2 * rp + 1], s1) : df_zero();
+        ws[2 * rp] = x0;
+        ws[2 * rp + 1] = x1;
+        if (UPD) {
+          if (g0 < dim) w[g0] = x0;
+          if (g0 + 1 < dim) w[g0 + 1] = x1;
+        }
+        if (!PROJ) {
+          nrm = df_fma(x0, x0, nrm);
+          nrm = df_fma(x1, x1, nrm);
+        }
+      }
+    }
+    __syncthreads();
+    if (PROJ) {  // 4 threads per column (quarters of 16 rows); column ncols is w.w
+      const int c = tid >> 2, qt = tid & 3;
+      if (c <= ncols) {
+        const float4* col = reinterpret_cast<const float4*>((c < ncols ? Qs + c * B_FRP : ws) + qt * (B_FR / 4));
+        const float4* wv = reinterpret_cast<const float4*>(ws + qt * (B_FR / 4));
+#pragma unroll
+        for (int i = 0; i < B_FR / 8; ++i) {
+          const float4 qv = col[i], xv = wv[i];
+          dacc_fma(acc, make_df(qv.x, qv.y), make_df(xv.x, xv.y));
+          dacc_fma(acc, make_df(qv.z, qv.w), make_df(xv.z, xv.w));
+        }
+        dacc_norm(acc);
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  if (PROJ) {
+    df64 v = dacc_val(acc);
+    v = df_add(v, shfl_xor_df(v, 1));
+    v = df_add(v, shfl_xor_df(v, 2));
+    const int c = tid >> 2;
+    if ((tid & 3) == 0 && c <= ncols) h_out[c] = v;
+  } else {
+    __shared__ df64 red[BT / 32];
+    nrm = warp_sum_df(nrm);
+    if ((tid & 31) == 0) red[tid >> 5] = nrm;
+    __syncthreads();
+    if (tid == 0) {
+      df64 t = df_zero();
+      for (int i = 0; i < BT / 32; ++i) t = df_add(t, red[i]);
+      *nrm_out = t;
+    }
+  }
+  __syncthreads();
+}
+
+// w <- (I - Q Q^T)^2 w; returns w.w (valid in all threads)
+SSA_D df64 cta_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, df64* h1, df64* h2, df64* scal_,
+                    df64* stbuf) {
+  if (ncols > 0) {
+    cta_cgs_pass<false, true>(Q, ldq, ncols, w, dim, nullptr, h1, nullptr, stbuf);
+    cta_cgs_pass<true, true>(Q, ldq, ncols, w, dim, h1, h2, nullptr, stbuf);
+    cta_cgs_pass<true, false>(Q, ldq, ncols, w, dim, h2, nullptr, scal_, stbuf);
+  } else {
+    cta_cgs_pass<true, false>(Q, ldq, 0, w, dim, h1, nullptr, scal_, stbuf);
+  }
+  return *scal_;
+}
+
+// ---------------------------------------------------------------- Ritz products
+// out[:, m] = sum_{i<r} Q[:, i] P[i, m], m < ncol (P column-major, leading dimension ldp)
+SSA_D void cta_ritz(const df64* Q, int64_t ldq, int r, const df64* P, int ldp, int ncol, df64* out, int64_t ldo,
+                    int64_t dim, df64* Ps) {
+  for (int e = threadIdx.x; e < r * ncol; e += BT) {
+    const int i = e % r, m = e / r;
+    Ps[i * B_MAXC + m] = P[(int64_t)m * ldp + i];
+  }
+  __syncthreads();
+  for (int m0 = 0; m0 < ncol; m0 += 16) {
+    for (int64_t row = threadIdx.x; row < dim; row += BT) {
+      dacc acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = dacc_zero();
+      for (int i = 0; i < r; ++i) {
+        const df64 q = Q[(int64_t)i * ldq + row];
+        const df64* pr = Ps + i * B_MAXC + m0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) dacc_fma(acc[j], q, pr[j]);
+        if ((i & 31) == 31) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) dacc_norm(acc[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (m0 + j < ncol) out[(int64_t)(m0 + j) * ldo + row] = dacc_val(acc[j]);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- the kernel
+template <class T, int MAXE>
+__global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* fbuf = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<df64>* dbuf = reinterpret_cast<cplx<df64>*>(smem_raw);
+  df64* stbuf = reinterpret_cast<df64*>(smem_raw);
+  __shared__ int s_item;
+  __shared__ df64 h1[B_MAXC + 2], h2[B_MAXC + 2];
+  __shared__ df64 sc_nrm, est;
+  __shared__ int conv;
+  __shared__ unsigned status;
+  const Slot sl = carve(cx, blockIdx.x);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(cx.next, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= cx.nseries) break;
+    const int si = cx.order[item];
+    const BSeries S = cx.ser[si];
+    Geom g{};
+    g.N = S.N;
+    g.L = S.Lw;
+    g.K = S.Kw;
+    g.M = (int64_t)2 << S.lg_n;
+    g.lg_n = S.lg_n;
+    g.tw = cx.tw;
+    g.lg_P = cx.lg_P;
+    g.tA = cx.tA;
+    g.tB = cx.tB;
+    g.tws = cx.tws;
+    g.twshift = cx.lg_Mmax - (S.lg_n + 1);
+    const double* f = cx.f + S.f_off;
+    const int d = S.d, kk = S.kk, k = S.k;
+    const int64_t Lw = S.Lw, Kw = S.Kw, ldu = cx.ldu, ldv = cx.ldv;
+    const int ldb = B_MAXC;
+    const uint64_t seed = cx.seed;  // same draws alone and in any batch
+    // spectrum
+    cta_spectrum(g, f, sl.chat, sl.fscr, dbuf);
+    // clear the projected matrix; state
+    for (int e = threadIdx.x; e < ldb * ldb; e += BT) sl.B[e] = df_zero();
+    if (threadIdx.x == 0) {
+      est = df_zero();
+      status = 0u;
+      conv = 0;
+    }
+    __syncthreads();
+    int cur = 0;
+    df64* U = sl.U[0];
+    df64* V = sl.V[0];
+    uint64_t stream_id = 0;
+    int matvecs = 0;
+    // normalise w into qcol with breakdown replacement (coefficient -> *bentry)
+    auto normalize = [&](df64* w, int64_t dim, df64 nrm2, df64* Qb, int64_t ldq, int ncols, df64* bentry) {
+      df64 beta = df_sqrt(nrm2);
+      const bool good = beta.hi > 1e-14f * est.hi && beta.hi > 0.f && isfinite(beta.hi);
+      if (!isfinite(beta.hi) && threadIdx.x == 0) status |= SSA_DEV_NONFINITE;
+      df64* qcol = Qb + (int64_t)ncols * ldq;
+      if (good) {
+        const df64 inv = df_div(make_df(1.f, 0.f), beta);
+        for (int64_t i = threadIdx.x; i < dim; i += BT) qcol[i] = df_mul(w[i], inv);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          *bentry = beta;
+          if (df_gt(beta, est)) est = beta;
+        }
+      } else {
+        for (int64_t i = threadIdx.x; i < dim; i += BT) w[i] = sm64_uniform_pm1(seed, stream_id, i);
+        __syncthreads();
+        const df64 n2 = cta_cgs2(Qb, ldq, ncols, w, dim, h1, h2, &sc_nrm, stbuf);
+        const df64 nb = df_sqrt(n2);
+        const bool alive = ncols < dim && nb.hi > 1e-6f * sqrtf((float)dim / 3.f);
+        const df64 inv = alive ? df_div(make_df(1.f, 0.f), nb) : df_zero();
+        for (int64_t i = threadIdx.x; i < dim; i += BT) qcol[i] = df_mul(w[i], inv);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          *bentry = df_zero();
+          status |= SSA_DEV_BREAKDOWN;
+        }
+      }
+      __syncthreads();
+    };
+    // p_0
+    for (int64_t i = threadIdx.x; i < Lw; i += BT) sl.y[i] = sm64_uniform_pm1(seed, stream_id, i);
+    ++stream_id;
+    __syncthreads();
+    {
+      const df64 n2 = cta_cgs2(U, ldu, 0, sl.y, Lw, h1, h2, &sc_nrm, stbuf);
+      normalize(sl.y, Lw, n2, U, ldu, 0, &sl.T[0]);
+    }
+    int r = 1, c = 0;
+    auto side = [&](bool vside) {
+      df64* Qb = vside ? V : U;
+      const int64_t ldq = vside ? ldv : ldu;
+      const int64_t dim = vside ? Kw : Lw;
+      const int ncols = vside ? c : r;
+      const df64* src = vside ? U + (int64_t)(r - 1) * ldu : V + (int64_t)(c - 1) * ldv;
+      df64* bentry = vside ? sl.B + (int64_t)(r - 1) * ldb + c : sl.B + (int64_t)r * ldb + (c - 1);
+      cta_matvec<T, MAXE>(g, vside ? 1 : 0, src, sl.y, sl.chat, fbuf);
+      ++matvecs;
+      const df64 n2 = cta_cgs2(Qb, ldq, ncols, sl.y, dim, h1, h2, &sc_nrm, stbuf);
+      normalize(sl.y, dim, n2, Qb, ldq, ncols, bentry);
+      ++stream_id;
+      if (vside) ++c;
+      else ++r;
+    };
+    int restarts = 0;
+    side(true);
+    for (;;) {
+      while (c < d + 1) {
+        side(false);
+        side(true);
+      }
+      const int cp = c - 1;
+      const int cc = cp + (cp & 1);
+      const bool pre = cp >= 16 && ((size_t)r * cp + (size_t)cp * cp) * 4 <= (size_t)B_SMEM;
+      if (pre) {
+        float* A32 = reinterpret_cast<float*>(smem_raw);
+        svd_precondition_body<BT>(sl.B, ldb, r, cp, sl.A, sl.W, sl.T, cc, 40, 2e-6f, A32, A32 + r * cp);
+        __syncthreads();
+      }
+      svd_jacobi_body<BT>(sl.B, ldb, r, cp, sl.A, sl.W, cc, sl.sigma, sl.P, sl.Q, sl.resid, sl.sigma_d, k, cx.tol,
+                          &conv, &est, &status, 60, 1e-13f, pre ? 1 : 0);
+      __syncthreads();
+      const int converged = conv;
+      __syncthreads();
+      if (converged || restarts >= cx.max_restarts || kk >= cp) break;
+      // thick restart
+      const int nxt = cur ^ 1;
+      cta_ritz(U, ldu, r, sl.P, r, kk, sl.U[nxt], ldu, Lw, stbuf);
+      cta_ritz(V, ldv, cp, sl.Q, cp, kk, sl.V[nxt], ldv, Kw, stbuf);
+      for (int64_t i = threadIdx.x; i < Kw; i += BT) sl.V[nxt][(int64_t)kk * ldv + i] = V[(int64_t)cp * ldv + i];
+      {
+        const df64 ar = sl.B[(int64_t)(r - 1) * ldb + cp];
+        __syncthreads();
+        for (int e = threadIdx.x; e < ldb * ldb; e += BT) sl.B[e] = df_zero();
+        __syncthreads();
+        for (int i = threadIdx.x; i < kk; i += BT) {
+          sl.B[(int64_t)i * ldb + i] = sl.sigma[i];
+          sl.B[(int64_t)i * ldb + kk] = df_mul(ar, sl.P[(int64_t)i * r + (r - 1)]);
+        }
+      }
+      __syncthreads();
+      cur = nxt;
+      U = sl.U[cur];
+      V = sl.V[cur];
+      r = kk;
+      c = kk + 1;
+      ++restarts;
+    }
+    // Ritz vectors of the k wanted triples into the other buffers
+    const int cp = c - 1;
+    df64* Uf = sl.U[cur ^ 1];
+    df64* Vf = sl.V[cur ^ 1];
+    cta_ritz(U, ldu, r, sl.P, r, k, Uf, ldu, Lw, stbuf);
+    cta_ritz(V, ldv, cp, sl.Q, cp, k, Vf, ldv, Kw, stbuf);
+    // sign rule on the user's left vectors, then doubles in user orientation
+    const df64* Uu = S.transposed ? Vf : Uf;
+    const int64_t ldus = S.transposed ? ldv : ldu;
+    const int64_t Lu = S.transposed ? Kw : Lw;
+    __shared__ float sb[BT / 32];
+    __shared__ int64_t sidx[BT / 32];
+    __shared__ int sgn[B_MAXC];
+    for (int j = 0; j < k; ++j) {
+      const df64* u = Uu + (int64_t)j * ldus;
+      df64 best = make_df(-1.f, 0.f);
+      int64_t bi = 0;
+      for (int64_t i = threadIdx.x; i < Lu; i += BT) {
+        const df64 a = df_abs(u[i]);
+        if (df_gt(a, best)) { best = a; bi = i; }
+      }
+      for (int m = 16; m; m >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, best.hi, m);
+        const float ol = __shfl_xor_sync(0xffffffffu, best.lo, m);
+        const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, m);
+        const df64 o = make_df(oh, ol);
+        if (df_gt(o, best) || (o.hi == best.hi && o.lo == best.lo && oi < bi)) { best = o; bi = oi; }
+      }
+      if ((threadIdx.x & 31) == 0) { sb[threadIdx.x >> 5] = best.hi + best.lo; sidx[threadIdx.x >> 5] = bi; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float bv = -1.f;
+        int64_t bj = 0;
+        for (int wv = 0; wv < BT / 32; ++wv)
+          if (sb[wv] > bv || (sb[wv] == bv && sidx[wv] < bj)) { bv = sb[wv]; bj = sidx[wv]; }
+        sgn[j] = u[bj].hi < 0.f ? -1 : 1;
+      }
+      __syncthreads();
+    }
+    double* oU = cx.out_U + S.out_u;
+    double* oV = cx.out_V + S.out_v;
+    const df64* srcU = S.transposed ? Vf : Uf;
+    const df64* srcV = S.transposed ? Uf : Vf;
+    const int64_t ldsu = S.transposed ? ldv : ldu, ldsv = S.transposed ? ldu : ldv;
+    for (int64_t e = threadIdx.x; e < S.L * (int64_t)k; e += BT) {
+      const int64_t j = e / S.L, i = e - j * S.L;
+      oU[e] = df_to_double(srcU[j * ldsu + i]) * sgn[j];
+    }
+    for (int64_t e = threadIdx.x; e < S.K * (int64_t)k; e += BT) {
+      const int64_t j = e / S.K, i = e - j * S.K;
+      oV[e] = df_to_double(srcV[j * ldsv + i]) * sgn[j];
+    }
+    for (int j = threadIdx.x; j < k; j += BT) {
+      cx.out_sigma[S.out_s + j] = sl.sigma_d[j];
+      cx.out_resid[S.out_s + j] = sl.resid[j];
+    }
+    if (threadIdx.x == 0) {
+      cx.out_info[4 * si + 0] = conv;
+      cx.out_info[4 * si + 1] = restarts;
+      cx.out_info[4 * si + 2] = matvecs;
+      cx.out_info[4 * si + 3] = (int)status;
+    }
+    __syncthreads();
+    (void)cp;
+  }
+}
+
+// ---------------------------------------------------------------- refinement
+// sigma_j <- u_j^T (X v_j) with native-FP64 FFT products (n <= 8192, one CTA
+// per series), then the triples are re-sorted if two nearly equal values
+// swapped.  Runs after k_batch_ssa and reuses its slots: the spectrum goes
+// to the slot's spectrum area, column permutations use its V basis area.
+struct BRefine {
+  const cplx<double>* tw;
+  const cplx<double>* tA;
+  const cplx<double>* tB;
+  int* next;
+};
+
+__global__ void __launch_bounds__(BT) k_batch_refine(BCtx cx, BRefine rf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<double>* buf = reinterpret_cast<cplx<double>*>(smem_raw);
+  __shared__ int s_item;
+  __shared__ double red[BT / 32];
+  __shared__ double sg[B_MAXC];
+  __shared__ int perm[B_MAXC];
+  __shared__ int sorted;
+  const Slot sl = carve(cx, blockIdx.x);
+  cplx<double>* chat = reinterpret_cast<cplx<double>*>(sl.chat);
+  double* tmp = reinterpret_cast<double*>(sl.V[0]);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(rf.next, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= cx.nseries) break;
+    const int si = cx.order[item];
+    const BSeries S = cx.ser[si];
+    Geom g{};
+    g.N = S.N;
+    g.L = S.Lw;
+    g.K = S.Kw;
+    g.M = (int64_t)2 << S.lg_n;
+    g.lg_n = S.lg_n;
+    g.tw64 = rf.tw;
+    g.lg_P = cx.lg_P;
+    g.tA64 = rf.tA;
+    g.tB64 = rf.tB;
+    g.tws = cx.tws;
+    g.twshift = cx.lg_Mmax - (S.lg_n + 1);
+    const double* f = cx.f + S.f_off;
+    const int n = 1 << g.lg_n;
+    const cplx<double> one = mk(1.0, 0.0);
+    // spectrum of the circulant column, scaled by 1/(4n)
+    for (int t = threadIdx.x; t < n; t += BT) buf[t] = mk(circ(g, f, 2 * (int64_t)t), circ(g, f, 2 * (int64_t)t + 1));
+    __syncthreads();
+    cta_fft<double, BT, 8192, false>(buf, g.lg_n, 1, g.tw64, g.lg_P);
+    const double sc = 0.5 / (4.0 * (double)n);
+    for (int kx = threadIdx.x; kx <= n / 2; kx += BT) {
+      const int nk = (n - kx) & (n - 1);
+      const cplx<double> tw = kx ? twiddle_M<double>(g.tA64, g.tB64, g.tws, (int64_t)kx << g.twshift) : one;
+      cplx<double> wk, wnk;
+      rfft_post(buf[kx], buf[nk], tw, wk, wnk);
+      chat[kx] = mk(wk.re * sc, wk.im * sc);
+      chat[n - kx] = mk(wnk.re * sc, wnk.im * sc);
+    }
+    __syncthreads();
+    const double* Ui = cx.out_U + S.out_u;  // user orientation, signs applied to u and v alike
+    const double* Vi = cx.out_V + S.out_v;
+    const int64_t ldUi = S.L, ldVi = S.K;
+    if (S.transposed) {  // working orientation: u in the user's V, v in the user's U
+      const double* t = Ui; Ui = Vi; Vi = t;
+    }
+    const int64_t ldu_w = S.transposed ? ldVi : ldUi, ldv_w = S.transposed ? ldUi : ldVi;
+    for (int j = 0; j < S.k; ++j) {
+      const double* v = Vi + (int64_t)j * ldv_w;
+      const double* u = Ui + (int64_t)j * ldu_w;
+      for (int t = threadIdx.x; t < n; t += BT) {
+        const int64_t j0 = 2 * (int64_t)t, j1 = j0 + 1;
+        buf[t] = mk(j0 < g.K ? v[g.K - 1 - j0] : 0.0, j1 < g.K ? v[g.K - 1 - j1] : 0.0);
+      }
+      __syncthreads();
+      cta_fft<double, BT, 8192, false>(buf, g.lg_n, 1, g.tw64, g.lg_P);
+      for (int kx = threadIdx.x; kx <= n / 2; kx += BT) {
+        const int nk = (n - kx) & (n - 1);
+        const cplx<double> tw = kx ? twiddle_M<double>(g.tA64, g.tB64, g.tws, (int64_t)kx << g.twshift) : one;
+        cplx<double> wk, wnk, zk, znk;
+        rfft_post(buf[kx], buf[nk], tw, wk, wnk);
+        irfft_pre(c_mul(wk, chat[kx]), c_mul(wnk, chat[n - kx]), tw, zk, znk);
+        buf[kx] = zk;
+        if (kx != 0 && nk != kx) buf[nk] = znk;
+      }
+      __syncthreads();
+      cta_fft<double, BT, 8192, true>(buf, g.lg_n, 1, g.tw64, g.lg_P);
+      double acc = 0.0;
+      for (int64_t m = threadIdx.x; m < g.L; m += BT) {
+        const cplx<double> z = buf[m >> 1];
+        acc = fma(u[m], (m & 1) ? z.im : z.re, acc);
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < BT / 32; ++w) t += red[w];
+        sg[j] = t;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {  // stable insertion sort, descending
+      sorted = 1;
+      for (int j = 0; j < S.k; ++j) perm[j] = j;
+      for (int j = 1; j < S.k; ++j) {
+        const int pj = perm[j];
+        int q = j;
+        while (q > 0 && sg[perm[q - 1]] < sg[pj]) {
+          perm[q] = perm[q - 1];
+          --q;
+        }
+        perm[q] = pj;
+        if (q != j) sorted = 0;
+      }
+    }
+    __syncthreads();
+    double* osig = cx.out_sigma + S.out_s;
+    double* ores = cx.out_resid + S.out_s;
+    if (sorted) {
+      for (int j = threadIdx.x; j < S.k; j += BT) osig[j] = sg[j];
+    } else {
+      for (int j = threadIdx.x; j < S.k; j += BT) tmp[j] = ores[j];
+      __syncthreads();
+      for (int j = threadIdx.x; j < S.k; j += BT) {
+        osig[j] = sg[perm[j]];
+        ores[j] = tmp[perm[j]];
+      }
+      __syncthreads();
+      double* cols[2] = {cx.out_U + S.out_u, cx.out_V + S.out_v};
+      const int64_t lens[2] = {S.L, S.K};
+      for (int a = 0; a < 2; ++a) {
+        const int64_t tot = lens[a] * S.k;
+        for (int64_t e = threadIdx.x; e < tot; e += BT) tmp[e] = cols[a][e];
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < tot; e += BT) {
+          const int64_t j = e / lens[a], i = e - j * lens[a];
+          cols[a][e] = tmp[(int64_t)perm[j] * lens[a] + i];
+        }
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0) cx.out_info[4 * si + 2] += S.k;
+    __syncthreads();
+  }
+}
+
+}  // namespace ssa
+
+using namespace ssa;
+
+// ---------------------------------------------------------------- host API
+struct ssa_batch_s {
+  int nseries = 0;
+  std::vector<BSeries> ser;
+  std::vector<int> info;  // 4 per series
+  double *U = nullptr, *V = nullptr, *sigma = nullptr, *resid = nullptr;
+  int64_t totU = 0, totV = 0, totS = 0;
+};
+
+static int bfail(int code, const char* msg) {
+  host_set_error(msg);
+  return code;
+}
+#define BCK(x)                                                         \
+  do {                                                                 \
+    cudaError_t e_ = (x);                                              \
+    if (e_ != cudaSuccess) {                                           \
+      char m_[256];                                                    \
+      std::snprintf(m_, sizeof m_, "%s: %s", #x, cudaGetErrorString(e_)); \
+      return bfail(e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA, m_); \
+    }                                                                  \
+  } while (0)
+
+static bool b_on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class X>
+static int to_host(const X* p, size_t n, std::vector<X>& out) {
+  out.resize(n);
+  if (b_on_device(p)) BCK(cudaMemcpy(out.data(), p, n * sizeof(X), cudaMemcpyDeviceToHost));
+  else std::memcpy(out.data(), p, n * sizeof(X));
+  return SSA_OK;
+}
+
+static cplx<double> b_tw64(int64_t m, int64_t P) {
+  m %= P;
+  const long double th = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)P;
+  return mk((double)cosl(th), -(double)sinl(th));
+}
+
+static cplx<df64> b_tw(int64_t m, int64_t P) {
+  m %= P;
+  const long double th = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)P;
+  cplx<df64> z;
+  z.re = df_from_double((double)cosl(th));
+  z.im = df_from_double(-(double)sinl(th));
+  return z;
+}
+
+extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* offsets, const int64_t* Ls,
+                                   const int32_t* ks, const ssa_opts_t* opts, ssa_batch_t* out) {
+  if (!out) return bfail(SSA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nseries < 1 || !f || !offsets || !Ls || !ks) return bfail(SSA_EINVAL, "need nseries >= 1 and non-NULL arrays");
+  ssa_opts_t o;
+  if (opts) o = *opts;
+  else ssa_default_opts(&o);
+  if (o.precision != SSA_PREC_F64 && o.precision != SSA_PREC_F32C) return bfail(SSA_EINVAL, "unknown precision");
+  const int64_t nmax_allowed = o.precision == SSA_PREC_F32C ? 32768 : 16384;
+  // native-FP64 Rayleigh quotients need N <= 16384 (the double FFT fits one CTA)
+  if (o.refine != SSA_REFINE_OFF && o.refine != SSA_REFINE_ON) return bfail(SSA_EINVAL, "unknown refine mode");
+  const bool refine = o.refine == SSA_REFINE_ON;
+  std::vector<int64_t> off, L;
+  std::vector<int32_t> kv;
+  int rc = to_host(offsets, (size_t)nseries + 1, off);
+  if (rc) return rc;
+  rc = to_host(Ls, (size_t)nseries, L);
+  if (rc) return rc;
+  rc = to_host(ks, (size_t)nseries, kv);
+  if (rc) return rc;
+  if (off[0] != 0) return bfail(SSA_EINVAL, "offsets[0] must be 0");
+  ssa_batch_s* b = new (std::nothrow) ssa_batch_s();
+  if (!b) return SSA_ENOMEM;
+  b->nseries = nseries;
+  b->ser.resize(nseries);
+  int64_t ldu = 4, ldv = 4;
+  int lgMmax = 2, nmax = 2;
+  for (int i = 0; i < nseries; ++i) {
+    BSeries& S = b->ser[i];
+    S.f_off = off[i];
+    S.N = off[i + 1] - off[i];
+    S.L = L[i];
+    S.K = S.N - S.L + 1;
+    char msg[160];
+    if (S.N <= 2 || S.N > (refine ? 16384 : nmax_allowed) || S.L <= 1 || S.L >= S.N) {
+      std::snprintf(msg, sizeof msg, "series %d: need 2 < N <= %lld and 1 < L < N", i,
+                    (long long)(refine ? 16384 : nmax_allowed));
+      delete b;
+      return bfail(SSA_EINVAL, msg);
+    }
+    S.transposed = S.L > S.K;
+    S.Lw = S.transposed ? S.K : S.L;
+    S.Kw = S.transposed ? S.L : S.K;
+    S.k = kv[i];
+    if (S.k < 1 || S.k > S.Lw) {
+      std::snprintf(msg, sizeof msg, "series %d: need 1 <= k <= min(L, K)", i);
+      delete b;
+      return bfail(SSA_EINVAL, msg);
+    }
+    int d = o.krylov_dim > 0 ? o.krylov_dim : std::max(2 * S.k, S.k + 32);
+    if (d > S.Lw) d = (int)S.Lw;
+    if (d < S.k) d = S.k;
+    if (d > B_MAXD) {
+      std::snprintf(msg, sizeof msg, "series %d: Krylov dimension %d above the batched limit %d", i, d, B_MAXD);
+      delete b;
+      return bfail(SSA_EINVAL, msg);
+    }
+    int kk = o.keep > 0 ? o.keep : S.k + (d - S.k + 1) / 2;
+    if (kk > d - 1) kk = d - 1;
+    if (kk < S.k) kk = S.k;
+    S.d = d;
+    S.kk = kk;
+    int64_t M = 4;
+    while (M < S.N) M *= 2;
+    int lg = 0;
+    while (((int64_t)1 << lg) < M) ++lg;
+    S.lg_n = lg - 1;
+    lgMmax = std::max(lgMmax, lg);
+    nmax = std::max(nmax, (int)(M / 2));
+    ldu = std::max(ldu, (S.Lw + 3) / 4 * 4);
+    ldv = std::max(ldv, (S.Kw + 3) / 4 * 4);
+    S.out_u = b->totU;
+    S.out_v = b->totV;
+    S.out_s = b->totS;
+    b->totU += S.L * S.k;
+    b->totV += S.K * S.k;
+    b->totS += S.k;
+  }
+  // work order: largest estimated cost first
+  std::vector<int> order(nseries);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c2) {
+    const double ca = (double)b->ser[a].N * b->ser[a].d * b->ser[a].d;
+    const double cb = (double)b->ser[c2].N * b->ser[c2].d * b->ser[c2].d;
+    return ca > cb;
+  });
+  // twiddle tables for the largest transform
+  const int64_t Mmax = (int64_t)1 << lgMmax;
+  const int lg_P = lgMmax - 1;
+  const int64_t P = (int64_t)1 << lg_P;
+  const int tws = (lgMmax + 1) / 2;
+  const int64_t nA = Mmax >> tws, nB = (int64_t)1 << tws;
+  std::vector<cplx<df64>> htw(P), hA(nA), hB(nB);
+  for (int64_t m = 0; m < P; ++m) htw[m] = b_tw(m, P);
+  for (int64_t m = 0; m < nA; ++m) hA[m] = b_tw(m << tws, Mmax);
+  for (int64_t m = 0; m < nB; ++m) hB[m] = b_tw(m, Mmax);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
+  int dev = 0, sms = 0;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int nslots = std::min(sms, nseries);
+  const int64_t sbytes = slot_bytes_for(ldu, ldv, nmax);
+  // device buffers
+  cplx<df64> *dtw = nullptr, *dA = nullptr, *dB = nullptr;
+  cplx<double> *dtw64 = nullptr, *dA64 = nullptr, *dB64 = nullptr;
+  BSeries* dser = nullptr;
+  int *dorder = nullptr, *dnext = nullptr, *dinfo = nullptr;
+  char* slots = nullptr;
+  double* fdev = nullptr;
+  bool own_f = false;
+  auto cleanup = [&]() {
+    cudaFree(dtw);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dtw64);
+    cudaFree(dA64);
+    cudaFree(dB64);
+    cudaFree(dser);
+    cudaFree(dorder);
+    cudaFree(dnext);
+    cudaFree(dinfo);
+    cudaFree(slots);
+    if (own_f) cudaFree(fdev);
+  };
+#define BCK2(x)                                                        \
+  do {                                                                 \
+    cudaError_t e_ = (x);                                              \
+    if (e_ != cudaSuccess) {                                           \
+      char m_[256];                                                    \
+      std::snprintf(m_, sizeof m_, "%s: %s", #x, cudaGetErrorString(e_)); \
+      cleanup();                                                       \
+      ssa_batch_destroy(b);                                            \
+      return bfail(e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA, m_); \
+    }                                                                  \
+  } while (0)
+  BCK2(cudaMalloc(&dtw, P * sizeof(cplx<df64>)));
+  BCK2(cudaMalloc(&dA, nA * sizeof(cplx<df64>)));
+  BCK2(cudaMalloc(&dB, nB * sizeof(cplx<df64>)));
+  BCK2(cudaMalloc(&dser, nseries * sizeof(BSeries)));
+  BCK2(cudaMalloc(&dorder, nseries * sizeof(int)));
+  BCK2(cudaMalloc(&dnext, 2 * sizeof(int)));
+  BCK2(cudaMalloc(&dinfo, 4 * (size_t)nseries * sizeof(int)));
+  BCK2(cudaMalloc(&slots, (size_t)nslots * sbytes));
+  BCK2(cudaMalloc(&b->U, std::max<int64_t>(b->totU, 1) * sizeof(double)));
+  BCK2(cudaMalloc(&b->V, std::max<int64_t>(b->totV, 1) * sizeof(double)));
+  BCK2(cudaMalloc(&b->sigma, std::max<int64_t>(b->totS, 1) * sizeof(double)));
+  BCK2(cudaMalloc(&b->resid, std::max<int64_t>(b->totS, 1) * sizeof(double)));
+  if (b_on_device(f)) {
+    fdev = const_cast<double*>(f);
+  } else {
+    BCK2(cudaMalloc(&fdev, off[nseries] * sizeof(double)));
+    own_f = true;
+    BCK2(cudaMemcpyAsync(fdev, f, off[nseries] * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  BCK2(cudaMemcpyAsync(dtw, htw.data(), P * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
+  BCK2(cudaMemcpyAsync(dA, hA.data(), nA * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
+  BCK2(cudaMemcpyAsync(dB, hB.data(), nB * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
+  BCK2(cudaMemcpyAsync(dser, b->ser.data(), nseries * sizeof(BSeries), cudaMemcpyHostToDevice, s));
+  BCK2(cudaMemcpyAsync(dorder, order.data(), nseries * sizeof(int), cudaMemcpyHostToDevice, s));
+  BCK2(cudaMemsetAsync(dnext, 0, 2 * sizeof(int), s));
+  if (refine) {
+    std::vector<cplx<double>> h64(std::max(P, std::max(nA, nB)));
+    BCK2(cudaMalloc(&dtw64, P * sizeof(cplx<double>)));
+    BCK2(cudaMalloc(&dA64, nA * sizeof(cplx<double>)));
+    BCK2(cudaMalloc(&dB64, nB * sizeof(cplx<double>)));
+    for (int64_t m = 0; m < P; ++m) h64[m] = b_tw64(m, P);
+    BCK2(cudaMemcpy(dtw64, h64.data(), P * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+    for (int64_t m = 0; m < nA; ++m) h64[m] = b_tw64(m << tws, Mmax);
+    BCK2(cudaMemcpy(dA64, h64.data(), nA * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+    for (int64_t m = 0; m < nB; ++m) h64[m] = b_tw64(m, Mmax);
+    BCK2(cudaMemcpy(dB64, h64.data(), nB * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+  }
+  BCK2(cudaMemsetAsync(slots, 0, (size_t)nslots * sbytes, s));
+  BCtx cx{};
+  cx.ser = dser;
+  cx.nseries = nseries;
+  cx.order = dorder;
+  cx.next = dnext;
+  cx.f = fdev;
+  cx.out_U = b->U;
+  cx.out_V = b->V;
+  cx.out_sigma = b->sigma;
+  cx.out_resid = b->resid;
+  cx.out_info = dinfo;
+  cx.tw = dtw;
+  cx.lg_P = lg_P;
+  cx.tA = dA;
+  cx.tB = dB;
+  cx.tws = tws;
+  cx.lg_Mmax = lgMmax;
+  cx.slots = slots;
+  cx.slot_bytes = sbytes;
+  cx.ldu = ldu;
+  cx.ldv = ldv;
+  cx.nmax = nmax;
+  cx.precision = o.precision;
+  cx.tol = o.tol > 0 ? o.tol : (o.precision == SSA_PREC_F32C ? 1e-7 * std::sqrt((double)lgMmax) : 1e-13);
+  cx.max_restarts = o.max_restarts;
+  cx.seed = o.seed;
+  prof_begin(s);
+  if (o.precision == SSA_PREC_F32C) {
+    auto kern = k_batch_ssa<float, 16384>;
+    BCK2(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
+    kern<<<nslots, BT, B_SMEM, s>>>(cx);
+  } else {
+    auto kern = k_batch_ssa<df64, 8192>;
+    BCK2(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
+    kern<<<nslots, BT, B_SMEM, s>>>(cx);
+  }
+  prof_end(s, K_BATCH, 0.0, 0.0);
+  BCK2(cudaGetLastError());
+  if (refine) {
+    BRefine rf{dtw64, dA64, dB64, dnext + 1};
+    BCK2(cudaFuncSetAttribute(k_batch_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
+    prof_begin(s);
+    k_batch_refine<<<nslots, BT, B_SMEM, s>>>(cx, rf);
+    prof_end(s, K_BATCH, 0.0, 0.0);
+    BCK2(cudaGetLastError());
+  }
+  b->info.resize(4 * (size_t)nseries);
+  BCK2(cudaMemcpyAsync(b->info.data(), dinfo, 4 * (size_t)nseries * sizeof(int), cudaMemcpyDeviceToHost, s));
+  BCK2(cudaStreamSynchronize(s));
+  cleanup();
+#undef BCK2
+  int worst = SSA_OK;
+  for (int i = 0; i < nseries; ++i) {
+    const unsigned st = (unsigned)b->info[4 * i + 3];
+    if (st & SSA_DEV_NONFINITE) worst = SSA_ENUMERIC;
+    else if (!b->info[4 * i] && worst == SSA_OK) worst = SSA_ENOCONV;
+  }
+  *out = b;
+  if (worst == SSA_ENUMERIC) host_set_error("non-finite value in a batched series");
+  if (worst == SSA_ENOCONV) host_set_error("a batched series did not converge within max_restarts");
+  return worst;
+}
+
+extern "C" int ssa_batch_info(ssa_batch_t b, int i, int* k, int* converged, int* restarts, int64_t* matvecs) {
+  if (!b || i < 0 || i >= b->nseries) return bfail(SSA_EINVAL, "bad batch handle or index");
+  if (k) *k = b->ser[i].k;
+  if (converged) *converged = b->info[4 * i];
+  if (restarts) *restarts = b->info[4 * i + 1];
+  if (matvecs) *matvecs = b->info[4 * i + 2];
+  return SSA_OK;
+}
+
+extern "C" int ssa_batch_get(ssa_batch_t b, int i, double* sigma, double* U, double* V, double* resid) {
+  if (!b || i < 0 || i >= b->nseries) return bfail(SSA_EINVAL, "bad batch handle or index");
+  const BSeries& S = b->ser[i];
+  if (sigma) BCK(cudaMemcpy(sigma, b->sigma + S.out_s, S.k * sizeof(double), cudaMemcpyDefault));
+  if (resid) BCK(cudaMemcpy(resid, b->resid + S.out_s, S.k * sizeof(double), cudaMemcpyDefault));
+  if (U) BCK(cudaMemcpy(U, b->U + S.out_u, (size_t)S.L * S.k * sizeof(double), cudaMemcpyDefault));
+  if (V) BCK(cudaMemcpy(V, b->V + S.out_v, (size_t)S.K * S.k * sizeof(double), cudaMemcpyDefault));
+  return SSA_OK;
+}
+
+extern "C" void ssa_batch_destroy(ssa_batch_t b) {
+  if (!b) return;
+  cudaFree(b->U);
+  cudaFree(b->V);
+  cudaFree(b->sigma);
+  cudaFree(b->resid);
+  delete b;
+}

@@ -104,6 +104,11 @@ SSA_HD float s_sub(float a, float b) { return a - b; }
 SSA_HD float s_mul(float a, float b) { return a * b; }
 SSA_HD float s_neg(float a) { return -a; }
 SSA_HD float s_scale(float a, float p2) { return a * p2; }
+SSA_HD double s_add(double a, double b) { return a + b; }
+SSA_HD double s_sub(double a, double b) { return a - b; }
+SSA_HD double s_mul(double a, double b) { return a * b; }
+SSA_HD double s_neg(double a) { return -a; }
+SSA_HD double s_scale(double a, float p2) { return a * (double)p2; }
 SSA_HD df64 s_add(df64 a, df64 b) { return df_add(a, b); }
 SSA_HD df64 s_sub(df64 a, df64 b) { return df_sub(a, b); }
 SSA_HD df64 s_mul(df64 a, df64 b) { return df_mul(a, b); }
@@ -124,6 +129,13 @@ template <> struct scal<df64> {
   SSA_HD static df64 to_df(df64 a) { return a; }
 };
 
+template <> struct scal<double> {
+  SSA_HD static double zero() { return 0.0; }
+  SSA_HD static double from_df(df64 a) { return (double)a.hi + (double)a.lo; }
+  SSA_HD static double from_double(double x) { return x; }
+  SSA_HD static df64 to_df(double a) { return df_from_double(a); }
+};
+
 template <class T> struct cplx {
   T re, im;
 };
@@ -139,18 +151,30 @@ template <class T> SSA_HD cplx<T> c_scale(cplx<T> a, float p2) { return mk(s_sca
 SSA_HD cplx<float> c_mul(cplx<float> a, cplx<float> b) {
   return mk(fmaf(a.re, b.re, -a.im * b.im), fmaf(a.re, b.im, a.im * b.re));
 }
+SSA_HD cplx<double> c_mul(cplx<double> a, cplx<double> b) {
+  return mk(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
 SSA_HD cplx<df64> c_mul(cplx<df64> a, cplx<df64> b) {
   return mk(df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re)));
 }
 // a * conj(b)
 template <class T> SSA_HD cplx<T> c_mul_conj(cplx<T> a, cplx<T> b) { return c_mul(a, c_conj(b)); }
 
-// Twiddle tables are stored in df64 (float2 pairs for re and im); FP32 code
-// reads the rounded value.
-template <class T> SSA_D cplx<T> tw_load(const cplx<df64>* tab, int64_t m);
+// Twiddle tables and spectra are stored in df64 (float2 pairs for re and im)
+// for the FP32 and df64 paths -- FP32 code reads the rounded value -- and in
+// IEEE double for the native-FP64 path.
+template <class T> struct tabt { using type = cplx<df64>; };
+template <> struct tabt<double> { using type = cplx<double>; };
+template <class T> using tab_t = typename tabt<T>::type;
+
+template <class T> SSA_D cplx<T> tw_load(const tab_t<T>* tab, int64_t m);
 template <> SSA_D cplx<df64> tw_load<df64>(const cplx<df64>* tab, int64_t m) {
   float4 v = __ldg(reinterpret_cast<const float4*>(tab) + m);
   return mk(make_df(v.x, v.y), make_df(v.z, v.w));
+}
+template <> SSA_D cplx<double> tw_load<double>(const cplx<double>* tab, int64_t m) {
+  double2 v = __ldg(reinterpret_cast<const double2*>(tab) + m);
+  return mk(v.x, v.y);
 }
 template <> SSA_D cplx<float> tw_load<float>(const cplx<df64>* tab, int64_t m) {
   float4 v = __ldg(reinterpret_cast<const float4*>(tab) + m);

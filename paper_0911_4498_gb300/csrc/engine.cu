@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -150,6 +151,12 @@ static cplx<df64> tw_entry(int64_t m, int64_t P) {
   return z;
 }
 
+static cplx<double> tw_entry64(int64_t m, int64_t P) {
+  double c, s;
+  cis_turn(m, P, c, s);
+  return mk(c, -s);
+}
+
 static int ilog2(int64_t x) {
   int r = 0;
   while (((int64_t)1 << r) < x) ++r;
@@ -172,7 +179,6 @@ struct Workspace {
   int* flag = nullptr;
   unsigned* status = nullptr;
   int* sgn = nullptr;
-  std::map<int, int2*> sched;
   void release() {
     for (int i = 0; i < 2; ++i) {
       cudaFree(Ub[i]);
@@ -200,8 +206,6 @@ struct Workspace {
     cudaFree(flag);
     cudaFree(status);
     cudaFree(sgn);
-    for (auto& kv : sched) cudaFree(kv.second);
-    sched.clear();
     B = y = est = dummy = nullptr;
     rw = ReorthWork{};
     sw = SvdWork{};
@@ -225,6 +229,11 @@ struct ssa_plan_s {
   cplx<df64>* chat = nullptr;
   void* scratch = nullptr;
   double* f_dev = nullptr;
+  // IEEE-double tables and spectrum for the Rayleigh-quotient refinement (made on first use)
+  cplx<double>* tw64 = nullptr;
+  cplx<double>* tA64 = nullptr;
+  cplx<double>* tB64 = nullptr;
+  cplx<double>* chat64 = nullptr;
   bool has_series = false;
   Workspace ws;
 };
@@ -246,7 +255,7 @@ struct ssa_decomp_s {
 namespace ssa {
 static const char* const kClassNames[K_NCLASS] = {
     "spectrum", "matvec_small", "matvec_colfwd", "matvec_row", "matvec_colinv", "cgs_proj", "cgs_update",
-    "cgs_update_proj", "normalize", "small_svd", "svd_precondition", "ritz", "hankel_small", "hankel_fourstep", "misc", "gated"};
+    "cgs_update_proj", "normalize", "small_svd", "svd_precondition", "ritz", "hankel_small", "hankel_fourstep", "misc", "gated", "batch_ssa"};
 struct PendingLaunch {
   int cls;
   cudaEvent_t a, b;
@@ -364,6 +373,7 @@ extern "C" void ssa_default_opts(ssa_opts_t* o) {
   o->keep = 0;
   o->seed = 0;
   o->stream = nullptr;
+  o->refine = SSA_REFINE_OFF;
 }
 
 extern "C" const char* ssa_strerror(int code) {
@@ -390,6 +400,10 @@ extern "C" void ssa_plan_destroy(ssa_plan_t p) {
   cudaFree(p->chat);
   cudaFree(p->scratch);
   cudaFree(p->f_dev);
+  cudaFree(p->tw64);
+  cudaFree(p->tA64);
+  cudaFree(p->tB64);
+  cudaFree(p->chat64);
   delete p;
 }
 
@@ -403,6 +417,7 @@ extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_
   if (opts) o = *opts;
   else ssa_default_opts(&o);
   REQ(o.precision == SSA_PREC_F64 || o.precision == SSA_PREC_F32C, "unknown precision %d", o.precision);
+  REQ(o.refine == SSA_REFINE_OFF || o.refine == SSA_REFINE_ON, "unknown refine mode %d", o.refine);
   ssa_plan_s* p = new (std::nothrow) ssa_plan_s();
   if (!p) return SSA_ENOMEM;
   p->opts = o;
@@ -597,33 +612,7 @@ static int ensure_workspace(ssa_plan_t p, int d) {
   return SSA_OK;
 }
 
-// Round-robin (circle method) schedule: cc-1 rounds of cc/2 disjoint pairs.
-static int get_schedule(Workspace& w, int c, const int2** out) {
-  auto it = w.sched.find(c);
-  if (it != w.sched.end()) {
-    *out = it->second;
-    return SSA_OK;
-  }
-  const int cc = c + (c & 1);
-  std::vector<int> pos(cc);
-  for (int i = 0; i < cc; ++i) pos[i] = i;
-  std::vector<int2> h;
-  h.reserve((size_t)(cc - 1) * (cc / 2));
-  for (int rnd = 0; rnd < cc - 1; ++rnd) {
-    for (int j = 0; j < cc / 2; ++j) h.push_back(make_int2(pos[j], pos[cc - 1 - j]));
-    const int last = pos[cc - 1];
-    for (int i = cc - 1; i >= 2; --i) pos[i] = pos[i - 1];
-    if (cc > 1) pos[1] = last;
-  }
-  int2* d = nullptr;
-  if (!h.empty()) {
-    CK(cudaMalloc(&d, h.size() * sizeof(int2)));
-    CK(cudaMemcpy(d, h.data(), h.size() * sizeof(int2), cudaMemcpyHostToDevice));
-  }
-  w.sched[c] = d;
-  *out = d;
-  return SSA_OK;
-}
+static int refine_sigma(ssa_plan_t p, ssa_decomp_s* res, int k);
 
 static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   const int prec = p->opts.precision;
@@ -693,10 +682,7 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
       if (rc) return rc;
     }
     const int cp = c - 1;
-    const int2* sched = nullptr;
-    rc = get_schedule(w, cp, &sched);
-    if (rc) return rc;
-    launch_small_svd(w.B, w.ldb, r, cp, sched, w.sw, k, tol, w.est, w.status, s);
+    launch_small_svd(w.B, w.ldb, r, cp, w.sw, k, tol, w.est, w.status, s);
     CHECK_LAUNCH();
     CK(cudaMemcpyAsync(&converged, w.sw.conv, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&status, w.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -753,10 +739,102 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   res->d = d;
   res->converged = converged;
   res->restarts = restarts;
+  if (p->opts.refine == SSA_REFINE_ON) {
+    rc = refine_sigma(p, res, k);
+    if (rc) return rc;
+    matvecs += k;
+  }
   res->matvecs = matvecs;
   // Uw / Vw keep the unsigned vectors: Hankelizing sigma u v^T does not
   // depend on flipping u and v together.
   return converged ? SSA_OK : SSA_ENOCONV;
+}
+
+// Native-FP64 tables and spectrum of the plan's series (the four-step order
+// is kept unless the native product runs in one CTA).
+static int native_spectrum(ssa_plan_t p, Geom& g64) {
+  Geom& g = p->g;
+  const int64_t P = (int64_t)1 << g.lg_P;
+  const int64_t M = g.M;
+  const int64_t nA = M >> g.tws, nB = (int64_t)1 << g.tws;
+  const int64_t n = (int64_t)1 << g.lg_n;
+  if (!p->tw64) {
+    std::vector<cplx<double>> htw(P), hA(nA), hB(nB);
+    for (int64_t m = 0; m < P; ++m) htw[m] = tw_entry64(m, P);
+    for (int64_t m = 0; m < nA; ++m) hA[m] = tw_entry64(m << g.tws, M);
+    for (int64_t m = 0; m < nB; ++m) hB[m] = tw_entry64(m, M);
+    CK(cudaMalloc(&p->tw64, P * sizeof(cplx<double>)));
+    CK(cudaMalloc(&p->tA64, nA * sizeof(cplx<double>)));
+    CK(cudaMalloc(&p->tB64, nB * sizeof(cplx<double>)));
+    CK(cudaMalloc(&p->chat64, (n + 1) * sizeof(cplx<double>)));
+    CK(cudaMemcpy(p->tw64, htw.data(), P * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->tA64, hA.data(), nA * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->tB64, hB.data(), nB * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+  }
+  g64 = g;
+  g64.tw64 = p->tw64;
+  g64.tA64 = p->tA64;
+  g64.tB64 = p->tB64;
+  const float scale = 1.0f / (4.0f * (float)n);
+  launch_spectrum64(g64, p->f_dev, p->chat64, native_small(g64) ? 1 : 0, scale, p->scratch, p->stream);
+  CHECK_LAUNCH();
+  return SSA_OK;
+}
+
+// sigma_i <- u_i^T (X v_i) with native-FP64 products, in chunks of vectors
+// (the four-step product needs n complex doubles of scratch per vector).
+// Returned triples are re-sorted if two nearly equal values swapped.
+static int refine_sigma(ssa_plan_t p, ssa_decomp_s* res, int k) {
+  Geom g64{};
+  int rc = native_spectrum(p, g64);
+  if (rc) return rc;
+  cudaStream_t s = p->stream;
+  const int64_t Lw = p->Lw, Kw = p->Kw;
+  const double* Ui = p->transposed ? res->V : res->U;  // working orientation, columns signed alike
+  const double* Vi = p->transposed ? res->U : res->V;
+  const int64_t n = (int64_t)1 << g64.lg_n;
+  const bool small = native_small(g64);
+  int chunk = small ? k : (int)std::max<int64_t>(1, std::min<int64_t>(k, ((int64_t)256 << 20) / (n * 16)));
+  double* Y = nullptr;
+  void* scr = nullptr;
+  CK(cudaMallocAsync(&Y, (size_t)Lw * chunk * sizeof(double), s));
+  if (!small && chunk > 1) CK(cudaMallocAsync(&scr, (size_t)n * chunk * sizeof(cplx<double>), s));
+  for (int c0 = 0; c0 < k; c0 += chunk) {
+    const int nb = std::min(chunk, k - c0);
+    launch_matvec_native(g64, 0, Vi + (int64_t)c0 * Kw, Kw, Y, Lw, nb, p->chat64, scr ? scr : p->scratch, s);
+    launch_col_dots(Ui + (int64_t)c0 * Lw, Lw, Y, Lw, Lw, nb, res->sigma + c0, s);
+  }
+  CHECK_LAUNCH();
+  if (scr) CK(cudaFreeAsync(scr, s));
+  CK(cudaFreeAsync(Y, s));
+  std::vector<double> sg(k);
+  CK(cudaMemcpyAsync(sg.data(), res->sigma, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  bool sorted = true;
+  for (int i = 1; i < k; ++i) sorted = sorted && sg[i - 1] >= sg[i];
+  if (sorted) return SSA_OK;
+  std::vector<int> perm(k);
+  for (int i = 0; i < k; ++i) perm[i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return sg[a] > sg[b]; });
+  auto permute = [&](void* base, size_t colbytes) -> int {
+    void* tmp = nullptr;
+    CK(cudaMallocAsync(&tmp, colbytes * k, s));
+    CK(cudaMemcpyAsync(tmp, base, colbytes * k, cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < k; ++i)
+      if (perm[i] != i)
+        CK(cudaMemcpyAsync(static_cast<char*>(base) + colbytes * i, static_cast<char*>(tmp) + colbytes * perm[i],
+                           colbytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaFreeAsync(tmp, s));
+    return SSA_OK;
+  };
+  if ((rc = permute(res->sigma, sizeof(double)))) return rc;
+  if ((rc = permute(res->resid, sizeof(double)))) return rc;
+  if ((rc = permute(res->U, p->L * sizeof(double)))) return rc;
+  if ((rc = permute(res->V, p->K * sizeof(double)))) return rc;
+  if ((rc = permute(res->Uw, Lw * sizeof(df64)))) return rc;
+  if ((rc = permute(res->Vw, Kw * sizeof(df64)))) return rc;
+  CK(cudaStreamSynchronize(s));
+  return SSA_OK;
 }
 
 extern "C" void ssa_decomp_destroy(ssa_decomp_t d) {

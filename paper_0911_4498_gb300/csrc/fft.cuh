@@ -43,7 +43,7 @@ SSA_D void bfly4(cplx<T>& x0, cplx<T>& x1, cplx<T>& x2, cplx<T>& x3) {
 
 // One Stockham stage of radix R.  ilog2 arguments avoid integer division.
 template <class T, int R, int THREADS, int MAXE, bool INV>
-SSA_D void fft_stage(cplx<T>* buf, int lg_len, int count, int lg_ns, const cplx<df64>* tw, int lg_P) {
+SSA_D void fft_stage(cplx<T>* buf, int lg_len, int count, int lg_ns, const tab_t<T>* tw, int lg_P) {
   constexpr int MAXB = (MAXE / R + THREADS - 1) / THREADS;
   const int lg_nbp = lg_len - (R == 4 ? 2 : 1);  // log2 butterflies per transform
   const int nb = count << lg_nbp;
@@ -94,7 +94,7 @@ SSA_D void fft_stage(cplx<T>* buf, int lg_len, int count, int lg_ns, const cplx<
 // Batched in-place FFT; caller must __syncthreads() before (data loaded) —
 // the routine ends with a barrier.
 template <class T, int THREADS, int MAXE, bool INV>
-SSA_D void cta_fft(cplx<T>* buf, int lg_len, int count, const cplx<df64>* tw, int lg_P) {
+SSA_D void cta_fft(cplx<T>* buf, int lg_len, int count, const tab_t<T>* tw, int lg_P) {
   int lg_ns = 0;
   while (lg_len - lg_ns >= 2) {
     fft_stage<T, 4, THREADS, MAXE, INV>(buf, lg_len, count, lg_ns, tw, lg_P);
@@ -129,7 +129,7 @@ SSA_D void irfft_pre(cplx<T> pk, cplx<T> pnk, cplx<T> twk, cplx<T>& zk, cplx<T>&
 
 // W_M^m from a two-level table: tA[m >> s] * tB[m & (2^s - 1)].
 template <class T>
-SSA_D cplx<T> twiddle_M(const cplx<df64>* tA, const cplx<df64>* tB, int s, int64_t m) {
+SSA_D cplx<T> twiddle_M(const tab_t<T>* tA, const tab_t<T>* tB, int s, int64_t m) {
   cplx<T> a = tw_load<T>(tA, m >> s);
   cplx<T> b = tw_load<T>(tB, m & ((1 << s) - 1));
   return c_mul(a, b);
@@ -143,5 +143,6 @@ SSA_D cplx<float> mul_spec(cplx<float> w, cplx<df64> c) {
   return mk(re, im);
 }
 SSA_D cplx<df64> mul_spec(cplx<df64> w, cplx<df64> c) { return c_mul(w, c); }
+SSA_D cplx<double> mul_spec(cplx<double> w, cplx<double> c) { return c_mul(w, c); }
 
 }  // namespace ssa

@@ -46,7 +46,7 @@ int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64
                           const df64* Q, int64_t ldq, int ncols, uint64_t seed, uint64_t stream, unsigned* status,
                           cudaStream_t s);
 void launch_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stream, cudaStream_t s);
-void launch_small_svd(const df64* B, int ldb, int r, int c, const int2* sched, SvdWork& sw, int k, double tol_conv,
+void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, double tol_conv,
                       df64* est, unsigned* status, cudaStream_t s);
 void launch_restart_B(df64* B, int ldb, int nrows_clear, const SvdWork& sw, int r, int kk, int c_old,
                       cudaStream_t s);
@@ -57,6 +57,9 @@ void launch_sign(const df64* U, int64_t ldu, int64_t dim, int k, int* sgn, cudaS
 void launch_store_cols(const df64* src, int64_t lds, int64_t dim, int ncol, const int* sgn, double* dst, int64_t ldd,
                        cudaStream_t s);
 void launch_df_to_double(const df64* src, double* dst, int64_t n, cudaStream_t s);
+// out[j] = sum_i A[j*lda + i] * B[j*ldb + i] over i < dim, in FP64 (one block per column)
+void launch_col_dots(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t dim, int ncol, double* out,
+                     cudaStream_t s);
 void launch_double_to_df(const double* src, int64_t lds, df64* dst, int64_t ldd, int64_t dim, int ncol,
                          cudaStream_t s);
 

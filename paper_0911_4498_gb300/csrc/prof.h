@@ -24,6 +24,7 @@ enum KClass {
   K_HANKEL_FS,
   K_MISC,
   K_GATED,
+  K_BATCH,
   K_NCLASS
 };
 

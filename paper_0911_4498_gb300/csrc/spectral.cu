@@ -31,6 +31,8 @@ SSA_D void st(df64* p, int64_t i, float v) { p[i] = make_df(v, 0.f); }
 SSA_D void st(df64* p, int64_t i, df64 v) { p[i] = v; }
 SSA_D void st(double* p, int64_t i, float v) { p[i] = (double)v; }
 SSA_D void st(double* p, int64_t i, df64 v) { p[i] = df_to_double(v); }
+SSA_D void st(double* p, int64_t i, double v) { p[i] = v; }
+SSA_D void st(df64* p, int64_t i, double v) { p[i] = df_from_double(v); }
 
 template <class T, int G, class In>
 SSA_D T gather(const Geom& g, const In* x, int64_t glen, int64_t j) {
@@ -45,6 +47,20 @@ SSA_D T gather(const Geom& g, const In* x, int64_t glen, int64_t j) {
 }
 
 template <class T> SSA_D cplx<T> c_one() { return mk(scal<T>::from_double(1.0), scal<T>::zero()); }
+// value of the arithmetic type T stored into a table of type tab_t<T>
+template <class T> SSA_D tab_t<T> to_tab(cplx<T> v) {
+  if constexpr (std::is_same<T, double>::value) return v;
+  else return mk(scal<T>::to_df(v.re), scal<T>::to_df(v.im));
+}
+template <class T> SSA_D cplx<T> from_tab(tab_t<T> v) {
+  if constexpr (std::is_same<T, double>::value) return v;
+  else return mk(scal<T>::from_df(v.re), scal<T>::from_df(v.im));
+}
+// o += q, accumulated in the table's precision
+template <class T> SSA_D void tab_acc(tab_t<T>& o, cplx<T> q) {
+  if constexpr (std::is_same<T, double>::value) o = c_add(o, q);
+  else o = mk(df_add(o.re, scal<T>::to_df(q.re)), df_add(o.im, scal<T>::to_df(q.im)));
+}
 
 SSA_D float cnt_recip_f(const Geom& g, int64_t t) {
   int64_t c = t + 1;
@@ -56,9 +72,11 @@ SSA_D float cnt_recip_f(const Geom& g, int64_t t) {
 template <class T> SSA_D T div_count(T v, float cnt);
 template <> SSA_D float div_count<float>(float v, float cnt) { return v / cnt; }
 template <> SSA_D df64 div_count<df64>(df64 v, float cnt) { return df_div(v, make_df(cnt, 0.f)); }
+template <> SSA_D double div_count<double>(double v, float cnt) { return v / (double)cnt; }
 template <class T> SSA_D T mul_scalar(T v, float s);
 template <> SSA_D float mul_scalar<float>(float v, float s) { return v * s; }
 template <> SSA_D df64 mul_scalar<df64>(df64 v, float s) { return df_mul_f(v, s); }
+template <> SSA_D double mul_scalar<double>(double v, float s) { return v * (double)s; }
 
 // ------------------------------------------------ single-CTA kernels
 // Fused X v / X^T u: gather -> FFT -> real post-process -> x c-hat ->
@@ -66,7 +84,7 @@ template <> SSA_D df64 mul_scalar<df64>(df64 v, float s) { return df_mul_f(v, s)
 template <class T, int THREADS, int MAXE, int G, class In, class Out>
 __global__ void __launch_bounds__(THREADS) k_matvec_small(Geom g, const In* __restrict__ x, int64_t ldx,
                                                           Out* __restrict__ y, int64_t ldy,
-                                                          const cplx<df64>* __restrict__ chat,
+                                                          const tab_t<T>* __restrict__ chat,
                                                           int64_t out_off, int64_t out_cnt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -76,10 +94,10 @@ __global__ void __launch_bounds__(THREADS) k_matvec_small(Geom g, const In* __re
   for (int t = threadIdx.x; t < n; t += THREADS)
     buf[t] = mk(gather<T, G>(g, x, 0, 2 * (int64_t)t), gather<T, G>(g, x, 0, 2 * (int64_t)t + 1));
   __syncthreads();
-  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n, 1, g.tw, g.lg_P);
+  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n, 1, g_tw<T>(g), g.lg_P);
   for (int k = threadIdx.x; k <= n / 2; k += THREADS) {
     const int nk = (n - k) & (n - 1);
-    cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
+    cplx<T> tw = k ? twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
     cplx<T> wk, wnk, zk, znk;
     rfft_post(buf[k], buf[nk], tw, wk, wnk);
     cplx<T> pk = mul_spec(wk, chat[k]);
@@ -89,7 +107,7 @@ __global__ void __launch_bounds__(THREADS) k_matvec_small(Geom g, const In* __re
     if (k != 0 && nk != k) buf[nk] = znk;
   }
   __syncthreads();
-  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n, 1, g.tw, g.lg_P);
+  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n, 1, g_tw<T>(g), g.lg_P);
   for (int64_t m = threadIdx.x; m < out_cnt; m += THREADS) {
     const int64_t i = out_off + m;
     const cplx<T> z = buf[i >> 1];
@@ -100,7 +118,7 @@ __global__ void __launch_bounds__(THREADS) k_matvec_small(Geom g, const In* __re
 // Half spectrum W_0..W_n of a real length-M input (natural order), times scale.
 template <class T, int THREADS, int MAXE, int G, class In>
 __global__ void __launch_bounds__(THREADS) k_rfft_small(Geom g, const In* __restrict__ x, int64_t ldx, int64_t glen,
-                                                        cplx<df64>* __restrict__ out, int64_t ldo, float scale) {
+                                                        tab_t<T>* __restrict__ out, int64_t ldo, float scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int n = 1 << g.lg_n;
@@ -109,17 +127,17 @@ __global__ void __launch_bounds__(THREADS) k_rfft_small(Geom g, const In* __rest
   for (int t = threadIdx.x; t < n; t += THREADS)
     buf[t] = mk(gather<T, G>(g, x, glen, 2 * (int64_t)t), gather<T, G>(g, x, glen, 2 * (int64_t)t + 1));
   __syncthreads();
-  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n, 1, g.tw, g.lg_P);
+  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n, 1, g_tw<T>(g), g.lg_P);
   const float s = 0.5f * scale;
   for (int k = threadIdx.x; k <= n / 2; k += THREADS) {
     const int nk = (n - k) & (n - 1);
-    cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
+    cplx<T> tw = k ? twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
     cplx<T> wk, wnk;
     rfft_post(buf[k], buf[nk], tw, wk, wnk);
     wk = c_scale(wk, s);
     wnk = c_scale(wnk, s);
-    out[k] = mk(scal<T>::to_df(wk.re), scal<T>::to_df(wk.im));
-    out[n - k] = mk(scal<T>::to_df(wnk.re), scal<T>::to_df(wnk.im));
+    out[k] = to_tab<T>(wk);
+    out[n - k] = to_tab<T>(wnk);
   }
 }
 
@@ -158,14 +176,14 @@ __global__ void __launch_bounds__(THREADS) k_hankel_small(Geom g, const df64* __
       bv[t] = mk(gather<T, GATHER_PAD>(g, v, g.K, j), gather<T, GATHER_PAD>(g, v, g.K, j + 1));
     }
     __syncthreads();
-    cta_fft<T, THREADS, MAXE, false>(bu, g.lg_n, 2, g.tw, g.lg_P);
+    cta_fft<T, THREADS, MAXE, false>(bu, g.lg_n, 2, g_tw<T>(g), g.lg_P);
     const T sg = scal<T>::from_double(sigma[comp]);
 #pragma unroll
     for (int q = 0; q < MAXK; ++q) {
       const int k = threadIdx.x + q * THREADS;
       if (k <= n / 2) {
         const int nk = (n - k) & (n - 1);
-        cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
+        cplx<T> tw = k ? twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
         cplx<T> uk, unk, vk, vnk;
         rfft_post(bu[k], bu[nk], tw, uk, unk);
         rfft_post(bv[k], bv[nk], tw, vk, vnk);
@@ -181,7 +199,7 @@ __global__ void __launch_bounds__(THREADS) k_hankel_small(Geom g, const df64* __
     const int k = threadIdx.x + q * THREADS;
     if (k <= n / 2) {
       const int nk = (n - k) & (n - 1);
-      cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
+      cplx<T> tw = k ? twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, (int64_t)(k) << g.twshift) : c_one<T>();
       cplx<T> zk, znk;
       irfft_pre(acc_k[q], acc_nk[q], tw, zk, znk);
       bu[k] = zk;
@@ -189,7 +207,7 @@ __global__ void __launch_bounds__(THREADS) k_hankel_small(Geom g, const df64* __
     }
   }
   __syncthreads();
-  cta_fft<T, THREADS, MAXE, true>(bu, g.lg_n, 1, g.tw, g.lg_P);
+  cta_fft<T, THREADS, MAXE, true>(bu, g.lg_n, 1, g_tw<T>(g), g.lg_P);
   // acc holds 4 sigma U V; irfft_pre doubles it; inverse FFT scales by n
   const float scale = 1.0f / (8.0f * (float)n);
   for (int64_t t = threadIdx.x; t < g.N; t += THREADS) {
@@ -219,13 +237,13 @@ __global__ void __launch_bounds__(THREADS) k_fs_col_fwd(Geom g, const In* __rest
     buf[(bb << g.lg_n1) + a] = mk(gather<T, G>(g, x, glen, 2 * t), gather<T, G>(g, x, glen, 2 * t + 1));
   }
   __syncthreads();
-  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n1, cb, g.tw, g.lg_P);
+  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n1, cb, g_tw<T>(g), g.lg_P);
   for (int e = threadIdx.x; e < E; e += THREADS) {
     const int bb = e & (cb - 1), c = e >> lg_cb;
     const int64_t b = b0 + bb;
     cplx<T> v = buf[(bb << g.lg_n1) + c];
     const int64_t m = (2 * ((b * c) & (n - 1)));
-    if (m) v = c_mul(v, twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(m) << g.twshift));
+    if (m) v = c_mul(v, twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, (int64_t)(m) << g.twshift));
     Y[((int64_t)c << g.lg_n2) + b] = v;
   }
   (void)n1;
@@ -247,11 +265,13 @@ __global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict_
       buf[e] = Y[((int64_t)row << g.lg_n2) + (e & (n2 - 1))];
     }
     __syncthreads();
-    cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n2, 2, g.tw, g.lg_P);
+    cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n2, 2, g_tw<T>(g), g.lg_P);
   }
   const int npairs = blockIdx.x == 0 ? n2 + 1 : n2;
-  const cplx<df64>* sin_ = ra.spec_in ? ra.spec_in + (int64_t)blockIdx.y * ra.ld_spec : nullptr;
-  cplx<df64>* sout = ra.spec_out ? ra.spec_out + (int64_t)blockIdx.y * ra.ld_spec : nullptr;
+  using TT = tab_t<T>;
+  const TT* chat = static_cast<const TT*>(ra.chat);
+  const TT* sin_ = ra.spec_in ? static_cast<const TT*>(ra.spec_in) + (int64_t)blockIdx.y * ra.ld_spec : nullptr;
+  TT* sout = ra.spec_out ? static_cast<TT*>(ra.spec_out) + (int64_t)blockIdx.y * ra.ld_spec : nullptr;
   for (int p = threadIdx.x; p < npairs; p += THREADS) {
     int sa, sb, ca, ea, cbr, eb;  // smem slots and (row, column) of the pair members
     if (blockIdx.x == 0) {
@@ -272,40 +292,33 @@ __global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict_
     // perm-layout positions (row-major c * n2 + e); the partner of k = 0 is index n
     const int64_t pa = ((int64_t)ca << g.lg_n2) + ea;
     const int64_t pb = k0 ? n : ((int64_t)cbr << g.lg_n2) + eb;
-    cplx<T> tw = k0 ? c_one<T>() : twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(k) << g.twshift);
+    cplx<T> tw = k0 ? c_one<T>() : twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, (int64_t)(k) << g.twshift);
     cplx<T> pk, pnk;
     if (MODE == ROW_INV_LOAD) {
-      const cplx<df64> a = sin_[pa], b = sin_[pb];
-      pk = mk(scal<T>::from_df(a.re), scal<T>::from_df(a.im));
-      pnk = mk(scal<T>::from_df(b.re), scal<T>::from_df(b.im));
+      pk = from_tab<T>(sin_[pa]);
+      pnk = from_tab<T>(sin_[pb]);
     } else {
       cplx<T> wk, wnk;
       rfft_post(buf[sa], buf[sb], tw, wk, wnk);
       if (MODE == ROW_MATVEC) {
-        pk = mul_spec(wk, ra.chat[pa]);
-        pnk = mul_spec(wnk, ra.chat[pb]);
+        pk = mul_spec(wk, chat[pa]);
+        pnk = mul_spec(wnk, chat[pb]);
       } else if (MODE == ROW_FWD_STORE) {
         const float s = 0.5f * ra.scale;
         wk = c_scale(wk, s);
         wnk = c_scale(wnk, s);
         const int64_t oa = ra.natural ? k : pa;
         const int64_t ob = ra.natural ? (k0 ? n : n - k) : pb;
-        sout[oa] = mk(scal<T>::to_df(wk.re), scal<T>::to_df(wk.im));
-        if (!(k != 0 && sa == sb)) sout[ob] = mk(scal<T>::to_df(wnk.re), scal<T>::to_df(wnk.im));
+        sout[oa] = to_tab<T>(wk);
+        if (!(k != 0 && sa == sb)) sout[ob] = to_tab<T>(wnk);
         continue;
       } else {  // ROW_FWD_MUL_ACC: spec_out += weight * spec_in * W
         const T sg = scal<T>::from_double(ra.weight[ra.weight_idx] * 0.5);
-        cplx<T> ua = mk(scal<T>::from_df(sin_[pa].re), scal<T>::from_df(sin_[pa].im));
-        cplx<T> ub = mk(scal<T>::from_df(sin_[pb].re), scal<T>::from_df(sin_[pb].im));
-        cplx<T> qa = c_mul(ua, wk), qb = c_mul(ub, wnk);
+        cplx<T> qa = c_mul(from_tab<T>(sin_[pa]), wk), qb = c_mul(from_tab<T>(sin_[pb]), wnk);
         qa = mk(s_mul(qa.re, sg), s_mul(qa.im, sg));
         qb = mk(s_mul(qb.re, sg), s_mul(qb.im, sg));
-        cplx<df64> oa = sout[pa];
-        sout[pa] = mk(df_add(oa.re, scal<T>::to_df(qa.re)), df_add(oa.im, scal<T>::to_df(qa.im)));
-        if (!(k != 0 && sa == sb)) {
-          cplx<df64> ob = sout[pb];
-          sout[pb] = mk(df_add(ob.re, scal<T>::to_df(qb.re)), df_add(ob.im, scal<T>::to_df(qb.im)));
-        }
+        tab_acc<T>(sout[pa], qa);
+        if (!(k != 0 && sa == sb)) tab_acc<T>(sout[pb], qb);
         continue;
       }
     }
@@ -316,13 +329,13 @@ __global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict_
   }
   if (MODE == ROW_FWD_STORE || MODE == ROW_FWD_MUL_ACC) return;
   __syncthreads();
-  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n2, 2, g.tw, g.lg_P);
+  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n2, 2, g_tw<T>(g), g.lg_P);
   for (int e = threadIdx.x; e < 2 * n2; e += THREADS) {
     const int row = e < n2 ? r0 : r1;
     const int64_t b = e & (n2 - 1);
     cplx<T> v = buf[e];
     const int64_t m = 2 * ((b * row) & (n - 1));
-    if (m) v = c_mul_conj(v, twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)(m) << g.twshift));
+    if (m) v = c_mul_conj(v, twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, (int64_t)(m) << g.twshift));
     Y[((int64_t)row << g.lg_n2) + b] = v;
   }
 }
@@ -346,7 +359,7 @@ __global__ void __launch_bounds__(THREADS) k_fs_col_inv(Geom g, const cplx<T>* _
     buf[(bb << g.lg_n1) + c] = Y[((int64_t)c << g.lg_n2) + b0 + bb];
   }
   __syncthreads();
-  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n1, cb, g.tw, g.lg_P);
+  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n1, cb, g_tw<T>(g), g.lg_P);
   for (int e = threadIdx.x; e < 2 * E; e += THREADS) {
     const int half = e & 1;
     const int ee = e >> 1;
@@ -376,6 +389,7 @@ static int lg2(int64_t x) {
 template <class T> struct Lim;
 template <> struct Lim<float> { static constexpr int MAXE = 16384; static constexpr int COLE = 4096; };
 template <> struct Lim<df64> { static constexpr int MAXE = 8192; static constexpr int COLE = 2048; };
+template <> struct Lim<double> { static constexpr int MAXE = 8192; static constexpr int COLE = 2048; };
 constexpr int TH = 512;
 constexpr int TH_COL = 256;
 constexpr int TH_ROW = 256;
@@ -463,7 +477,7 @@ static void fs_inverse(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int
 
 template <class T, class In, class Out>
 static void matvec_impl(const Geom& g, int transpose, const In* x, int64_t ldx, Out* y, int64_t ldy, int batch,
-                        const cplx<df64>* chat, void* scratch, bool small, cudaStream_t s) {
+                        const tab_t<T>* chat, void* scratch, bool small, cudaStream_t s) {
   const int64_t off = transpose ? g.M - g.K : 0;
   const int64_t cnt = transpose ? g.K : g.L;
   // algorithmic traffic of a product (section 8(d)): the input and output
@@ -515,6 +529,14 @@ void launch_matvec_d(const Geom& g, int prec, int transpose, const double* x, in
   else matvec_impl<df64, double, double>(g, transpose, x, ldx, y, ldy, batch, chat, scratch, sm, s);
 }
 
+bool native_small(const Geom& g) { return ((int64_t)1 << g.lg_n) <= Lim<double>::MAXE; }
+
+void launch_matvec_native(const Geom& g, int transpose, const double* x, int64_t ldx, double* y, int64_t ldy,
+                          int batch, const cplx<double>* chat, void* scratch, cudaStream_t s) {
+  const bool sm = native_small(g);
+  matvec_impl<double, double, double>(g, transpose, x, ldx, y, ldy, batch, chat, scratch, sm, s);
+}
+
 // Spectrum of the circulant column, always in df64.  natural: 1 -> index k,
 // 0 -> four-step row-major order (c * n2 + e) with W_n at index n.
 void launch_spectrum(const Geom& g, const double* f, cplx<df64>* chat, int natural, float scale, void* scratch,
@@ -535,6 +557,26 @@ void launch_spectrum(const Geom& g, const double* f, cplx<df64>* chat, int natur
   ra.natural = natural;
   ra.scale = scale;
   fs_row<df64, ROW_FWD_STORE>(g, Y, ra, 1, s, K_SPECTRUM, 16.0 * (double)((1 << g.lg_n) + 1));
+}
+
+void launch_spectrum64(const Geom& g, const double* f, cplx<double>* chat, int natural, float scale, void* scratch,
+                       cudaStream_t s) {
+  if (native_small(g)) {
+    const size_t sm = (size_t)(1 << g.lg_n) * sizeof(cplx<double>);
+    auto kern = k_rfft_small<double, TH, Lim<double>::MAXE, GATHER_CIRC, double>;
+    set_smem(kern, sm);
+    prof_begin(s);
+    kern<<<1, TH, sm, s>>>(g, f, 0, 0, chat, 0, scale);
+    prof_end(s, K_SPECTRUM, 8.0 * g.N + 16.0 * (double)((1 << g.lg_n) + 1), 0.0);
+    return;
+  }
+  cplx<double>* Y = reinterpret_cast<cplx<double>*>(scratch);
+  fs_forward<double, GATHER_CIRC, double>(g, f, 0, 0, Y, 1, s, K_SPECTRUM, 8.0 * g.N);
+  RowArgs ra{};
+  ra.spec_out = chat;
+  ra.natural = natural;
+  ra.scale = scale;
+  fs_row<double, ROW_FWD_STORE>(g, Y, ra, 1, s, K_SPECTRUM, 16.0 * (double)((1 << g.lg_n) + 1));
 }
 
 template <class T, class Out>

@@ -1,10 +1,11 @@
 // Host-side interface of the spectral kernels (spectral.cu).
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 
 namespace ssa {
 
-enum { PREC_F64 = 0, PREC_F32C = 1 };
+enum { PREC_F64 = 0, PREC_F32C = 1, PREC_NATIVE64 = 2 };
 enum { GATHER_X = 0, GATHER_XT = 1, GATHER_CIRC = 2, GATHER_PAD = 3 };
 enum { ROW_MATVEC = 0, ROW_FWD_STORE = 1, ROW_FWD_MUL_ACC = 2, ROW_INV_LOAD = 3 };
 enum { OUT_SLICE = 0, OUT_HANKEL = 1 };
@@ -22,12 +23,29 @@ struct Geom {
   const cplx<df64>* tB;
   int tws;
   int twshift;  // the two-level table is for M << twshift (batched series share the largest table)
+  // IEEE-double copies of the tables for the native-FP64 products (may be null)
+  const cplx<double>* tw64;
+  const cplx<double>* tA64;
+  const cplx<double>* tB64;
 };
 
+// table pointers of the arithmetic type T
+template <class T> SSA_HD const tab_t<T>* g_tw(const Geom& g) {
+  if constexpr (std::is_same<T, double>::value) return g.tw64; else return g.tw;
+}
+template <class T> SSA_HD const tab_t<T>* g_tA(const Geom& g) {
+  if constexpr (std::is_same<T, double>::value) return g.tA64; else return g.tA;
+}
+template <class T> SSA_HD const tab_t<T>* g_tB(const Geom& g) {
+  if constexpr (std::is_same<T, double>::value) return g.tB64; else return g.tB;
+}
+
+// Spectrum pointers are of the table type tab_t<T> of the kernel's arithmetic
+// type T (double-float for FP32 and df64 arithmetic, double for native FP64).
 struct RowArgs {
-  const cplx<df64>* chat;      // ROW_MATVEC: scaled spectrum, four-step order
-  const cplx<df64>* spec_in;   // ROW_FWD_MUL_ACC / ROW_INV_LOAD input spectrum
-  cplx<df64>* spec_out;        // ROW_FWD_STORE / ROW_FWD_MUL_ACC output spectrum
+  const void* chat;            // ROW_MATVEC: scaled spectrum, four-step order
+  const void* spec_in;         // ROW_FWD_MUL_ACC / ROW_INV_LOAD input spectrum
+  void* spec_out;              // ROW_FWD_STORE / ROW_FWD_MUL_ACC output spectrum
   int64_t ld_spec;             // batch stride of spec_in / spec_out
   int natural;                 // ROW_FWD_STORE: natural index order (else four-step)
   float scale;                 // ROW_FWD_STORE: multiply W by this power of two
@@ -43,6 +61,14 @@ void launch_matvec_d(const Geom& g, int prec, int transpose, const double* x, in
                      int batch, const cplx<df64>* chat, void* scratch, cudaStream_t s);
 void launch_spectrum(const Geom& g, const double* f, cplx<df64>* chat, int natural, float scale, void* scratch,
                      cudaStream_t s);
+// native-FP64 spectrum (double tables), natural order or four-step order as above
+void launch_spectrum64(const Geom& g, const double* f, cplx<double>* chat, int natural, float scale, void* scratch,
+                       cudaStream_t s);
+// the native-FP64 product runs in one CTA (else four-step, n complex doubles of scratch per vector)
+bool native_small(const Geom& g);
+// y_j = X x_j in native FP64 with the double spectrum (Rayleigh-quotient refinement)
+void launch_matvec_native(const Geom& g, int transpose, const double* x, int64_t ldx, double* y, int64_t ldy,
+                          int batch, const cplx<double>* chat, void* scratch, cudaStream_t s);
 void launch_hankel(const Geom& g, int prec, const df64* U, int64_t ldu, const df64* V, int64_t ldv,
                    const double* sigma, const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
                    const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, cudaStream_t s);

@@ -124,3 +124,31 @@ def test_bad_k_rejected():
         gpu_decompose(synth.three_sines(100, 1), 40, 41)
     with pytest.raises(ssa.SSAError):
         gpu_decompose(synth.three_sines(100, 1), 40, 0)
+
+
+@pytest.mark.parametrize("N,L,k", [(5000, 2500, 16), (40000, 13333, 12)])
+def test_rayleigh_refinement(N, L, k):
+    """With refinement each sigma_i is u_i^T X v_i of the returned vectors,
+    computed with native-FP64 products: one CTA (n <= 8192) and four-step
+    (n = 32768) products, F64 and F32C; values stay sorted and within the
+    precision's tolerance; k extra products are counted."""
+    from oracle import fast_hankel
+    f = synth.many_sines(N, seed=3)
+    ref = ossa.decompose(f, L, k, method="lanczos")
+    for prec, tol in ((ssa.SSA_PREC_F64, SIG_F64), (ssa.SSA_PREC_F32C, SIG_F32C)):
+        got = gpu_decompose(f, L, k, precision=prec, refine=ssa.SSA_REFINE_ON)
+        chat = fast_hankel.spectrum(f, L, fast_hankel.fft_length(N))
+        XV = np.stack([fast_hankel.hankel_matvec(chat, N, L, got["V"][:, i]) for i in range(k)], axis=1)
+        rq = np.einsum("ij,ij->j", got["U"], XV)
+        assert np.max(np.abs(got["sigma"] - rq)) <= 1e-12 * got["sigma"][0], prec
+        assert np.max(_rel(got["sigma"], ref["sigma"])) <= tol, prec
+        assert np.all(np.diff(got["sigma"]) <= 0)
+    off = gpu_decompose(f, L, k)
+    on = gpu_decompose(f, L, k, refine=ssa.SSA_REFINE_ON)
+    assert on["info"]["matvecs"] == off["info"]["matvecs"] + k
+    assert np.max(_rel(off["sigma"], on["sigma"])) <= SIG_F64
+
+
+def test_bad_refine_mode_rejected():
+    with pytest.raises(ssa.SSAError):
+        gpu_decompose(synth.three_sines(100, 1), 40, 3, refine=7)
