@@ -64,10 +64,11 @@ typedef struct ssa_decomp_s* ssa_decomp_t;
 
 typedef struct ssa_opts {
   int precision;      /* SSA_PREC_F64 or SSA_PREC_F32C */
-  double tol;         /* convergence: every wanted Ritz residual <= tol * sigma_1 (0 = default for the precision) */
+  double tol;         /* convergence: every wanted Ritz residual <= tol * sigma_1 (0 = the precision's default:
+                         1e-12 for SSA_PREC_F64, 1e-7 sqrt(log2 M) for SSA_PREC_F32C) */
   int max_restarts;   /* thick restarts before SSA_ENOCONV (default 200) */
   int krylov_dim;     /* Krylov dimension d (0 = min(max(2k, k+32), min(L, K)); at most 510) */
-  int keep;           /* Ritz pairs kept per restart (0 = k + ceil((d-k)/2)) */
+  int keep;           /* Ritz pairs kept per restart (0 = k + ceil((d-k)/5)) */
   uint64_t seed;      /* splitmix64 seed of the starting vector p_0 and breakdown vectors */
   void* stream;       /* cudaStream_t for all GPU work (NULL = default stream) */
   int refine;         /* SSA_REFINE_ON: return each sigma_i as the Rayleigh quotient u_i^T X v_i of the
@@ -173,7 +174,8 @@ typedef struct ssa_batch_s* ssa_batch_t;
  *   Ls, ks:   window and number of triples per series (nseries each)
  *   opts:     as for plans; opts->krylov_dim / keep apply to every series.
  * Limits: N <= 32768 (SSA_PREC_F32C) or N <= 16384 (SSA_PREC_F64); Krylov
- * dimension min(max(2k, k+32), min(L, K)) <= 72, so k <= 40.
+ * dimension min(max(2k, k+32), min(L, K)) <= 72, so k <= 36 unless min(L, K) <= 72.
+ * With opts->refine = SSA_REFINE_ON every series needs N <= 16384.
  * On SSA_OK or SSA_ENOCONV (some series not converged) *out holds the results.
  * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ENOCONV, SSA_ENUMERIC, SSA_ECUDA.
  */
@@ -187,6 +189,73 @@ int ssa_batch_info(ssa_batch_t b, int i, int* k, int* converged, int* restarts, 
 int ssa_batch_get(ssa_batch_t b, int i, double* sigma, double* U, double* V, double* resid);
 
 void ssa_batch_destroy(ssa_batch_t b);
+
+/* ---- request server (continuous batching; not a step of the paper) ------ */
+
+/*
+ * A server decomposes series submitted at any time (ssa_decompose's truncated
+ * SVD, Algorithms 1-3) while earlier requests are still running.  Requests are
+ * admitted first-come-first-served as workers and the device-memory budget
+ * free up.  Requests that fit the batched engine (ssa_decompose_batch limits)
+ * are packed, as many as are queued (up to max_batch), into one persistent
+ * launch; the others run the single-series path, several at once.  Every
+ * worker has its own CUDA stream, so admitted requests overlap on the device.
+ * Each request's spectrum and Lanczos state stay on the device until its
+ * results are copied to host memory owned by the server.
+ * Threads: all ssa_serve_* calls may be made from any host thread.
+ */
+typedef struct ssa_server_s* ssa_server_t;
+
+typedef struct ssa_serve_opts {
+  int precision;        /* SSA_PREC_F64 or SSA_PREC_F32C for every request (default SSA_PREC_F32C) */
+  double tol;           /* as ssa_opts_t.tol (0 = the precision's default) */
+  int64_t mem_budget;   /* device bytes that admitted requests may hold together (default 40 GiB) */
+  int workers;          /* single-series requests running at once (default 8, at most 64) */
+  int batch_workers;    /* batched launches running at once (default 2, at most 16; 0 = never batch) */
+  int max_batch;        /* requests per batched launch (default 512) */
+  int64_t batch_max_n;  /* only series with N <= this are batched (0 = the engine's limit, -1 = none) */
+} ssa_serve_opts_t;
+
+#define SSA_SERVE_VECTORS 1  /* ssa_serve_submit outputs flag: keep U and V (else sigma and residuals only) */
+
+typedef struct ssa_serve_info {
+  int status;           /* SSA_OK, SSA_ENOCONV or the error of this request */
+  int converged, restarts;
+  int64_t matvecs;
+  int batched;          /* 1 if it ran in a batched launch */
+  double t_submit, t_start, t_done;  /* seconds since ssa_serve_create */
+} ssa_serve_info_t;
+
+typedef struct ssa_serve_stats {
+  int64_t submitted, completed, queued, running;
+  int64_t mem_in_use, mem_peak;  /* admitted device bytes (estimates), now and at the peak */
+  int64_t batches, batched_requests;
+} ssa_serve_stats_t;
+
+/* Defaults: SSA_PREC_F32C, tol 0, 40 GiB, 8 workers, 2 batch workers, max_batch 512, batch_max_n 0. */
+void ssa_serve_default_opts(ssa_serve_opts_t* opts);
+/* Start the worker threads.  opts may be NULL (defaults).  Errors: SSA_EINVAL, SSA_ENOMEM. */
+int ssa_serve_create(const ssa_serve_opts_t* opts, ssa_server_t* out);
+/*
+ * Queue one request: f (N doubles, host memory, copied before returning),
+ * window L and k triples; outputs = 0 or SSA_SERVE_VECTORS.  *id names it.
+ * Errors: SSA_EINVAL (sizes as ssa_embed_plan / ssa_decompose), SSA_ENOMEM
+ * (the request alone needs more than the memory budget).
+ */
+int ssa_serve_submit(ssa_server_t srv, const double* f, int64_t N, int64_t L, int k, int outputs, int64_t* id);
+/* *done = 1 once request id has finished; waits up to timeout_s seconds (0 = do not wait). */
+int ssa_serve_poll(ssa_server_t srv, int64_t id, double timeout_s, int* done);
+/*
+ * Copy a finished request's results to host buffers -- sigma (k), U (L x k),
+ * V (K x k), resid (k), each may be NULL; U and V only if SSA_SERVE_VECTORS
+ * was given -- fill *info (may be NULL) and release the request.  Returns
+ * the request's status (SSA_OK, SSA_ENOCONV with results, or its error).
+ */
+int ssa_serve_take(ssa_server_t srv, int64_t id, double* sigma, double* U, double* V, double* resid,
+                   ssa_serve_info_t* info);
+int ssa_serve_stats(ssa_server_t srv, ssa_serve_stats_t* stats);
+/* Finish the running requests, drop the queued ones and stop the threads. */
+void ssa_serve_destroy(ssa_server_t srv);
 
 /* ---- launch accounting (not part of the paper's method) ---------------- */
 
@@ -246,6 +315,8 @@ uint64_t ssa_kernel_launches(void);
 int ssa_matvec_noalloc(const double* f, int64_t N, int64_t L, int transpose, const double* x, double* y,
                        int precision, void* stream);
 
+/* Destroy decompositions before the plan they came from (their memory is
+ * released in the order of the plan's stream). */
 void ssa_plan_destroy(ssa_plan_t plan);
 void ssa_decomp_destroy(ssa_decomp_t d);
 const char* ssa_strerror(int code);

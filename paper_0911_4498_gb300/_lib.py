@@ -32,6 +32,26 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("mem_budget", ctypes.c_int64),
+                ("workers", ctypes.c_int), ("batch_workers", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("batch_max_n", ctypes.c_int64)]
+
+
+class ServeInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("converged", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("matvecs", ctypes.c_int64), ("batched", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "queued", "running", "mem_in_use",
+                                              "mem_peak", "batches", "batched_requests")]
+
+
+SSA_SERVE_VECTORS = 1
+
+
 class SSAError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{msg} (status {code})")
@@ -61,6 +81,13 @@ _SIGS = {
                             ctypes.POINTER(_I64)]),
     "ssa_batch_get": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "ssa_batch_destroy": (None, [_VP]),
+    "ssa_serve_default_opts": (None, [ctypes.POINTER(ServeOpts)]),
+    "ssa_serve_create": (_I, [ctypes.POINTER(ServeOpts), ctypes.POINTER(_VP)]),
+    "ssa_serve_submit": (_I, [_VP, _VP, _I64, _I64, _I, _I, ctypes.POINTER(_I64)]),
+    "ssa_serve_poll": (_I, [_VP, _I64, _D, ctypes.POINTER(_I)]),
+    "ssa_serve_take": (_I, [_VP, _I64, _VP, _VP, _VP, _VP, ctypes.POINTER(ServeInfo)]),
+    "ssa_serve_stats": (_I, [_VP, ctypes.POINTER(ServeStats)]),
+    "ssa_serve_destroy": (None, [_VP]),
     "ssa_stats_enable": (_I, [_I]),
     "ssa_stats_get": (_I, [ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "ssa_kernel_launches": (ctypes.c_uint64, []),
@@ -216,6 +243,56 @@ def ssa_batch_get(b, i: int, sigma=None, U=None, V=None, resid=None):
 
 def ssa_batch_destroy(b):
     lib().ssa_batch_destroy(b)
+
+
+def ssa_serve_default_opts() -> ServeOpts:
+    o = ServeOpts()
+    lib().ssa_serve_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_serve_opts(**kw) -> ServeOpts:
+    o = ssa_serve_default_opts()
+    for key, val in kw.items():
+        setattr(o, key, val)
+    return o
+
+
+def ssa_serve_create(opts: ServeOpts | None = None):
+    h = _VP()
+    _check(lib().ssa_serve_create(ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
+    return h
+
+
+def ssa_serve_submit(srv, f, L: int, k: int, outputs: int = 0) -> int:
+    """Queue f (host float64 array); returns the request id."""
+    rid = _I64()
+    _check(lib().ssa_serve_submit(srv, _ptr(f), int(f.size), L, k, outputs, ctypes.byref(rid)))
+    return rid.value
+
+
+def ssa_serve_poll(srv, rid: int, timeout_s: float = 0.0) -> bool:
+    done = _I()
+    _check(lib().ssa_serve_poll(srv, rid, timeout_s, ctypes.byref(done)))
+    return bool(done.value)
+
+
+def ssa_serve_take(srv, rid: int, sigma=None, U=None, V=None, resid=None):
+    """Copy results into the given host arrays; returns (status, info dict)."""
+    info = ServeInfo()
+    rc = _check(lib().ssa_serve_take(srv, rid, _ptr(sigma), _ptr(U), _ptr(V), _ptr(resid), ctypes.byref(info)),
+                allow=(SSA_ENOCONV,))
+    return rc, {n: getattr(info, n) for n, _ in ServeInfo._fields_}
+
+
+def ssa_serve_stats(srv) -> dict:
+    st = ServeStats()
+    _check(lib().ssa_serve_stats(srv, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in ServeStats._fields_}
+
+
+def ssa_serve_destroy(srv):
+    lib().ssa_serve_destroy(srv)
 
 
 def ssa_stats_enable(on: bool):

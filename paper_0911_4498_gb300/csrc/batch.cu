@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "ssa.h"
+#include "budget.h"
 #include "fft.cuh"
 #include "lanczos_dev.cuh"
 #include "prof.h"
@@ -98,6 +99,47 @@ int64_t slot_bytes_for(int64_t ldu, int64_t ldv, int nmax) {
   int64_t dfs = 2 * ldu * B_MAXC + 2 * ldv * B_MAXC + 6 * B_MAXC * B_MAXC + (B_MAXC + 2) + ldv;
   int64_t bytes = dfs * 8 + (int64_t)(2 * nmax + 2) * 16 + 2 * (B_MAXC + 2) * 8;
   return (bytes + 255) / 256 * 256;
+}
+
+static int b_krylov_dim(int64_t Lw, int k) {
+  int d = std::max(2 * k, k + 32);
+  if (d > Lw) d = (int)Lw;
+  if (d < k) d = k;
+  return d;
+}
+
+bool batch_eligible(int64_t N, int64_t L, int k, int precision) {
+  const int64_t K = N - L + 1;
+  const int64_t Lw = L < K ? L : K;
+  const int64_t nmax = precision == SSA_PREC_F32C ? 32768 : 16384;
+  return N > 2 && N <= nmax && L > 1 && L < N && k >= 1 && k <= Lw && b_krylov_dim(Lw, k) <= B_MAXD;
+}
+
+int64_t batch_path_bytes(const std::vector<BatchItem>& items, int refine) {
+  int64_t ldu = 4, ldv = 4, tot = 0, Mmax = 4;
+  int nmax = 2;
+  for (const BatchItem& it : items) {
+    const int64_t K = it.N - it.L + 1;
+    const int64_t Lw = it.L < K ? it.L : K, Kw = it.L < K ? K : it.L;
+    int64_t M = 4;
+    while (M < it.N) M *= 2;
+    Mmax = std::max(Mmax, M);
+    nmax = std::max(nmax, (int)(M / 2));
+    ldu = std::max(ldu, (Lw + 3) / 4 * 4);
+    ldv = std::max(ldv, (Kw + 3) / 4 * 4);
+    tot += (it.L + K) * it.k * 8 + it.k * 16 + it.N * 8 + (int64_t)sizeof(BSeries) + 24;
+  }
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 152;
+  }
+  const int64_t nslots = std::min<int64_t>(sms, (int64_t)items.size());
+  tot += nslots * slot_bytes_for(ldu, ldv, nmax);
+  tot += (Mmax / 2 + 2 * Mmax) * 16 * (refine ? 2 : 1);  // twiddle tables
+  return tot + (2 << 20);
 }
 
 // ---------------------------------------------------------------- spectrum
@@ -728,6 +770,7 @@ struct ssa_batch_s {
   std::vector<int> info;  // 4 per series
   double *U = nullptr, *V = nullptr, *sigma = nullptr, *resid = nullptr;
   int64_t totU = 0, totV = 0, totS = 0;
+  cudaStream_t stream = nullptr;  // outputs are stream-ordered allocations on this stream
 };
 
 static int bfail(int code, const char* msg) {
@@ -826,7 +869,7 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
       delete b;
       return bfail(SSA_EINVAL, msg);
     }
-    int d = o.krylov_dim > 0 ? o.krylov_dim : std::max(2 * S.k, S.k + 32);
+    int d = o.krylov_dim > 0 ? o.krylov_dim : b_krylov_dim(S.Lw, S.k);
     if (d > S.Lw) d = (int)S.Lw;
     if (d < S.k) d = S.k;
     if (d > B_MAXD) {
@@ -834,7 +877,7 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
       delete b;
       return bfail(SSA_EINVAL, msg);
     }
-    int kk = o.keep > 0 ? o.keep : S.k + (d - S.k + 1) / 2;
+    int kk = o.keep > 0 ? o.keep : S.k + (d - S.k + 4) / 5;
     if (kk > d - 1) kk = d - 1;
     if (kk < S.k) kk = S.k;
     S.d = d;
@@ -874,6 +917,7 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
   for (int64_t m = 0; m < nA; ++m) hA[m] = b_tw(m << tws, Mmax);
   for (int64_t m = 0; m < nB; ++m) hB[m] = b_tw(m, Mmax);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
+  b->stream = s;
   int dev = 0, sms = 0;
   BCK(cudaGetDevice(&dev));
   BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -888,18 +932,18 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
   double* fdev = nullptr;
   bool own_f = false;
   auto cleanup = [&]() {
-    cudaFree(dtw);
-    cudaFree(dA);
-    cudaFree(dB);
-    cudaFree(dtw64);
-    cudaFree(dA64);
-    cudaFree(dB64);
-    cudaFree(dser);
-    cudaFree(dorder);
-    cudaFree(dnext);
-    cudaFree(dinfo);
-    cudaFree(slots);
-    if (own_f) cudaFree(fdev);
+    if (dtw) cudaFreeAsync(dtw, s);
+    if (dA) cudaFreeAsync(dA, s);
+    if (dB) cudaFreeAsync(dB, s);
+    if (dtw64) cudaFreeAsync(dtw64, s);
+    if (dA64) cudaFreeAsync(dA64, s);
+    if (dB64) cudaFreeAsync(dB64, s);
+    if (dser) cudaFreeAsync(dser, s);
+    if (dorder) cudaFreeAsync(dorder, s);
+    if (dnext) cudaFreeAsync(dnext, s);
+    if (dinfo) cudaFreeAsync(dinfo, s);
+    if (slots) cudaFreeAsync(slots, s);
+    if (own_f && fdev) cudaFreeAsync(fdev, s);
   };
 #define BCK2(x)                                                        \
   do {                                                                 \
@@ -912,22 +956,22 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
       return bfail(e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA, m_); \
     }                                                                  \
   } while (0)
-  BCK2(cudaMalloc(&dtw, P * sizeof(cplx<df64>)));
-  BCK2(cudaMalloc(&dA, nA * sizeof(cplx<df64>)));
-  BCK2(cudaMalloc(&dB, nB * sizeof(cplx<df64>)));
-  BCK2(cudaMalloc(&dser, nseries * sizeof(BSeries)));
-  BCK2(cudaMalloc(&dorder, nseries * sizeof(int)));
-  BCK2(cudaMalloc(&dnext, 2 * sizeof(int)));
-  BCK2(cudaMalloc(&dinfo, 4 * (size_t)nseries * sizeof(int)));
-  BCK2(cudaMalloc(&slots, (size_t)nslots * sbytes));
-  BCK2(cudaMalloc(&b->U, std::max<int64_t>(b->totU, 1) * sizeof(double)));
-  BCK2(cudaMalloc(&b->V, std::max<int64_t>(b->totV, 1) * sizeof(double)));
-  BCK2(cudaMalloc(&b->sigma, std::max<int64_t>(b->totS, 1) * sizeof(double)));
-  BCK2(cudaMalloc(&b->resid, std::max<int64_t>(b->totS, 1) * sizeof(double)));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dtw), P * sizeof(cplx<df64>), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dA), nA * sizeof(cplx<df64>), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dB), nB * sizeof(cplx<df64>), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dser), nseries * sizeof(BSeries), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dorder), nseries * sizeof(int), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dnext), 2 * sizeof(int), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dinfo), 4 * (size_t)nseries * sizeof(int), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&slots), (size_t)nslots * sbytes, s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->U), std::max<int64_t>(b->totU, 1) * sizeof(double), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->V), std::max<int64_t>(b->totV, 1) * sizeof(double), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->sigma), std::max<int64_t>(b->totS, 1) * sizeof(double), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->resid), std::max<int64_t>(b->totS, 1) * sizeof(double), s));
   if (b_on_device(f)) {
     fdev = const_cast<double*>(f);
   } else {
-    BCK2(cudaMalloc(&fdev, off[nseries] * sizeof(double)));
+    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&fdev), off[nseries] * sizeof(double), s));
     own_f = true;
     BCK2(cudaMemcpyAsync(fdev, f, off[nseries] * sizeof(double), cudaMemcpyHostToDevice, s));
   }
@@ -939,15 +983,15 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
   BCK2(cudaMemsetAsync(dnext, 0, 2 * sizeof(int), s));
   if (refine) {
     std::vector<cplx<double>> h64(std::max(P, std::max(nA, nB)));
-    BCK2(cudaMalloc(&dtw64, P * sizeof(cplx<double>)));
-    BCK2(cudaMalloc(&dA64, nA * sizeof(cplx<double>)));
-    BCK2(cudaMalloc(&dB64, nB * sizeof(cplx<double>)));
+    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dtw64), P * sizeof(cplx<double>), s));
+    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dA64), nA * sizeof(cplx<double>), s));
+    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dB64), nB * sizeof(cplx<double>), s));
     for (int64_t m = 0; m < P; ++m) h64[m] = b_tw64(m, P);
-    BCK2(cudaMemcpy(dtw64, h64.data(), P * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+    BCK2(cudaMemcpyAsync(dtw64, h64.data(), P * sizeof(cplx<double>), cudaMemcpyHostToDevice, s));
     for (int64_t m = 0; m < nA; ++m) h64[m] = b_tw64(m << tws, Mmax);
-    BCK2(cudaMemcpy(dA64, h64.data(), nA * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+    BCK2(cudaMemcpyAsync(dA64, h64.data(), nA * sizeof(cplx<double>), cudaMemcpyHostToDevice, s));
     for (int64_t m = 0; m < nB; ++m) h64[m] = b_tw64(m, Mmax);
-    BCK2(cudaMemcpy(dB64, h64.data(), nB * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+    BCK2(cudaMemcpyAsync(dB64, h64.data(), nB * sizeof(cplx<double>), cudaMemcpyHostToDevice, s));
   }
   BCK2(cudaMemsetAsync(slots, 0, (size_t)nslots * sbytes, s));
   BCtx cx{};
@@ -973,7 +1017,7 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
   cx.ldv = ldv;
   cx.nmax = nmax;
   cx.precision = o.precision;
-  cx.tol = o.tol > 0 ? o.tol : (o.precision == SSA_PREC_F32C ? 1e-7 * std::sqrt((double)lgMmax) : 1e-13);
+  cx.tol = o.tol > 0 ? o.tol : (o.precision == SSA_PREC_F32C ? 1e-7 * std::sqrt((double)lgMmax) : 1e-12);
   cx.max_restarts = o.max_restarts;
   cx.seed = o.seed;
   prof_begin(s);
@@ -1025,18 +1069,18 @@ extern "C" int ssa_batch_info(ssa_batch_t b, int i, int* k, int* converged, int*
 extern "C" int ssa_batch_get(ssa_batch_t b, int i, double* sigma, double* U, double* V, double* resid) {
   if (!b || i < 0 || i >= b->nseries) return bfail(SSA_EINVAL, "bad batch handle or index");
   const BSeries& S = b->ser[i];
-  if (sigma) BCK(cudaMemcpy(sigma, b->sigma + S.out_s, S.k * sizeof(double), cudaMemcpyDefault));
-  if (resid) BCK(cudaMemcpy(resid, b->resid + S.out_s, S.k * sizeof(double), cudaMemcpyDefault));
-  if (U) BCK(cudaMemcpy(U, b->U + S.out_u, (size_t)S.L * S.k * sizeof(double), cudaMemcpyDefault));
-  if (V) BCK(cudaMemcpy(V, b->V + S.out_v, (size_t)S.K * S.k * sizeof(double), cudaMemcpyDefault));
+  cudaStream_t s = b->stream;
+  if (sigma) BCK(cudaMemcpyAsync(sigma, b->sigma + S.out_s, S.k * sizeof(double), cudaMemcpyDefault, s));
+  if (resid) BCK(cudaMemcpyAsync(resid, b->resid + S.out_s, S.k * sizeof(double), cudaMemcpyDefault, s));
+  if (U) BCK(cudaMemcpyAsync(U, b->U + S.out_u, (size_t)S.L * S.k * sizeof(double), cudaMemcpyDefault, s));
+  if (V) BCK(cudaMemcpyAsync(V, b->V + S.out_v, (size_t)S.K * S.k * sizeof(double), cudaMemcpyDefault, s));
+  BCK(cudaStreamSynchronize(s));
   return SSA_OK;
 }
 
 extern "C" void ssa_batch_destroy(ssa_batch_t b) {
   if (!b) return;
-  cudaFree(b->U);
-  cudaFree(b->V);
-  cudaFree(b->sigma);
-  cudaFree(b->resid);
+  for (double* ptr : {b->U, b->V, b->sigma, b->resid})
+    if (ptr) cudaFreeAsync(ptr, b->stream);
   delete b;
 }

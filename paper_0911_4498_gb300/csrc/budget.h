@@ -1,0 +1,21 @@
+// Device-memory estimates used for admission by the request server: the
+// bytes one decomposition holds on the device while it runs.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace ssa {
+
+// ssa_embed_plan + ssa_decompose of one series (default Krylov dimension)
+int64_t plan_path_bytes(int64_t N, int64_t L, int k, int precision);
+
+// one ssa_decompose_batch call over the given series (N, L, k each)
+struct BatchItem {
+  int64_t N, L;
+  int k;
+};
+int64_t batch_path_bytes(const std::vector<BatchItem>& items, int refine);
+// a series can run in the batched engine
+bool batch_eligible(int64_t N, int64_t L, int k, int precision);
+
+}  // namespace ssa

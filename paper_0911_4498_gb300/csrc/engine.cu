@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ssa.h"
+#include "budget.h"
 #include "lanczos.h"
 #include "spectral.h"
 #include "prof.h"
@@ -163,6 +164,16 @@ static int ilog2(int64_t x) {
   return r;
 }
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// plan's stream): creating and destroying plans and decompositions never
+// synchronises the device, so requests on other streams keep running.
+static void free_async(void* ptr, cudaStream_t s) {
+  if (ptr) cudaFreeAsync(ptr, s);
+}
+template <class T> static cudaError_t malloc_async(T** ptr, size_t bytes, cudaStream_t s) {
+  return cudaMallocAsync(reinterpret_cast<void**>(ptr), bytes, s);
+}
+
 // ------------------------------------------------------------------ handles
 struct Workspace {
   int dcap = 0;
@@ -179,33 +190,33 @@ struct Workspace {
   int* flag = nullptr;
   unsigned* status = nullptr;
   int* sgn = nullptr;
-  void release() {
+  void release(cudaStream_t st) {
     for (int i = 0; i < 2; ++i) {
-      cudaFree(Ub[i]);
-      cudaFree(Vb[i]);
+      free_async(Ub[i], st);
+      free_async(Vb[i], st);
       Ub[i] = Vb[i] = nullptr;
     }
-    cudaFree(B);
-    cudaFree(y);
-    cudaFree(rw.part);
-    cudaFree(rw.part2);
-    cudaFree(rw.coop);
-    cudaFree(rw.h);
-    cudaFree(rw.nrm);
-    cudaFree(rw.counter);
-    cudaFree(sw.A);
-    cudaFree(sw.W);
-    cudaFree(sw.sigma);
-    cudaFree(sw.P);
-    cudaFree(sw.Q);
-    cudaFree(sw.resid);
-    cudaFree(sw.sigma_d);
-    cudaFree(sw.conv);
-    cudaFree(est);
-    cudaFree(dummy);
-    cudaFree(flag);
-    cudaFree(status);
-    cudaFree(sgn);
+    free_async(B, st);
+    free_async(y, st);
+    free_async(rw.part, st);
+    free_async(rw.part2, st);
+    free_async(rw.coop, st);
+    free_async(rw.h, st);
+    free_async(rw.nrm, st);
+    free_async(rw.counter, st);
+    free_async(sw.A, st);
+    free_async(sw.W, st);
+    free_async(sw.sigma, st);
+    free_async(sw.P, st);
+    free_async(sw.Q, st);
+    free_async(sw.resid, st);
+    free_async(sw.sigma_d, st);
+    free_async(sw.conv, st);
+    free_async(est, st);
+    free_async(dummy, st);
+    free_async(flag, st);
+    free_async(status, st);
+    free_async(sgn, st);
     B = y = est = dummy = nullptr;
     rw = ReorthWork{};
     sw = SvdWork{};
@@ -392,18 +403,17 @@ extern "C" const char* ssa_last_error(void) { return g_err; }
 
 extern "C" void ssa_plan_destroy(ssa_plan_t p) {
   if (!p) return;
-  cudaStreamSynchronize(p->stream);
-  p->ws.release();
-  cudaFree(p->tw);
-  cudaFree(p->tA);
-  cudaFree(p->tB);
-  cudaFree(p->chat);
-  cudaFree(p->scratch);
-  cudaFree(p->f_dev);
-  cudaFree(p->tw64);
-  cudaFree(p->tA64);
-  cudaFree(p->tB64);
-  cudaFree(p->chat64);
+  p->ws.release(p->stream);
+  free_async(p->tw, p->stream);
+  free_async(p->tA, p->stream);
+  free_async(p->tB, p->stream);
+  free_async(p->chat, p->stream);
+  free_async(p->scratch, p->stream);
+  free_async(p->f_dev, p->stream);
+  free_async(p->tw64, p->stream);
+  free_async(p->tA64, p->stream);
+  free_async(p->tB64, p->stream);
+  free_async(p->chat64, p->stream);
   delete p;
 }
 
@@ -461,15 +471,15 @@ extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_
       return fail(e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA); \
     }                                           \
   } while (0)
-  PK(cudaMalloc(&p->tw, P * sizeof(cplx<df64>)));
-  PK(cudaMalloc(&p->tA, nA * sizeof(cplx<df64>)));
-  PK(cudaMalloc(&p->tB, nB * sizeof(cplx<df64>)));
-  PK(cudaMalloc(&p->chat, (n + 1) * sizeof(cplx<df64>)));
-  PK(cudaMalloc(&p->scratch, spectral_scratch_bytes(g)));
-  PK(cudaMalloc(&p->f_dev, N * sizeof(double)));
-  PK(cudaMemcpy(p->tw, htw.data(), P * sizeof(cplx<df64>), cudaMemcpyHostToDevice));
-  PK(cudaMemcpy(p->tA, hA.data(), nA * sizeof(cplx<df64>), cudaMemcpyHostToDevice));
-  PK(cudaMemcpy(p->tB, hB.data(), nB * sizeof(cplx<df64>), cudaMemcpyHostToDevice));
+  PK(malloc_async(&p->tw, P * sizeof(cplx<df64>), p->stream));
+  PK(malloc_async(&p->tA, nA * sizeof(cplx<df64>), p->stream));
+  PK(malloc_async(&p->tB, nB * sizeof(cplx<df64>), p->stream));
+  PK(malloc_async(&p->chat, (n + 1) * sizeof(cplx<df64>), p->stream));
+  PK(malloc_async(&p->scratch, spectral_scratch_bytes(g), p->stream));
+  PK(malloc_async(&p->f_dev, N * sizeof(double), p->stream));
+  PK(cudaMemcpyAsync(p->tw, htw.data(), P * sizeof(cplx<df64>), cudaMemcpyHostToDevice, p->stream));
+  PK(cudaMemcpyAsync(p->tA, hA.data(), nA * sizeof(cplx<df64>), cudaMemcpyHostToDevice, p->stream));
+  PK(cudaMemcpyAsync(p->tB, hB.data(), nB * sizeof(cplx<df64>), cudaMemcpyHostToDevice, p->stream));
 #undef PK
   g.tw = p->tw;
   g.tA = p->tA;
@@ -568,7 +578,8 @@ extern "C" int ssa_matvec(ssa_plan_t p, int transpose, const double* x, double* 
 static int ensure_workspace(ssa_plan_t p, int d) {
   Workspace& w = p->ws;
   if (w.dcap >= d) return SSA_OK;
-  w.release();
+  cudaStream_t st = p->stream;
+  w.release(st);
   const int cols = d + 2;
   w.ldu = (p->Lw + 3) / 4 * 4;
   w.ldv = (p->Kw + 3) / 4 * 4;
@@ -576,38 +587,38 @@ static int ensure_workspace(ssa_plan_t p, int d) {
   const int64_t dimmax = p->Kw > p->Lw ? p->Kw : p->Lw;
   const int G = reorth_blocks(dimmax);
   for (int i = 0; i < 2; ++i) {
-    CK(cudaMalloc(&w.Ub[i], (size_t)w.ldu * cols * sizeof(df64)));
-    CK(cudaMalloc(&w.Vb[i], (size_t)w.ldv * cols * sizeof(df64)));
-    CK(cudaMemset(w.Ub[i], 0, (size_t)w.ldu * cols * sizeof(df64)));
-    CK(cudaMemset(w.Vb[i], 0, (size_t)w.ldv * cols * sizeof(df64)));
+    CK(malloc_async(&w.Ub[i], (size_t)w.ldu * cols * sizeof(df64), st));
+    CK(malloc_async(&w.Vb[i], (size_t)w.ldv * cols * sizeof(df64), st));
+    CK(cudaMemsetAsync(w.Ub[i], 0, (size_t)w.ldu * cols * sizeof(df64), st));
+    CK(cudaMemsetAsync(w.Vb[i], 0, (size_t)w.ldv * cols * sizeof(df64), st));
   }
-  CK(cudaMalloc(&w.B, (size_t)w.ldb * w.ldb * sizeof(df64)));
-  CK(cudaMalloc(&w.y, (size_t)((dimmax + 3) / 4 * 4) * sizeof(df64)));
+  CK(malloc_async(&w.B, (size_t)w.ldb * w.ldb * sizeof(df64), st));
+  CK(malloc_async(&w.y, (size_t)((dimmax + 3) / 4 * 4) * sizeof(df64), st));
   w.rw.ldp = MAXCOL + 1;
-  CK(cudaMalloc(&w.rw.part, (size_t)G * w.rw.ldp * sizeof(df64)));
+  CK(malloc_async(&w.rw.part, (size_t)G * w.rw.ldp * sizeof(df64), st));
   w.rw.ldp2 = FUSED_MAXCOL + 1;
-  CK(cudaMalloc(&w.rw.part2, (size_t)fused_tiles(dimmax) * w.rw.ldp2 * sizeof(df64)));
+  CK(malloc_async(&w.rw.part2, (size_t)fused_tiles(dimmax) * w.rw.ldp2 * sizeof(df64), st));
   reorth_setup();
-  CK(cudaMalloc(&w.rw.coop, (size_t)coop_blocks() * (MAXCOL + 1) * sizeof(df64)));
-  CK(cudaMalloc(&w.rw.h, (MAXCOL + 1) * sizeof(df64)));
-  CK(cudaMalloc(&w.rw.nrm, sizeof(df64)));
-  CK(cudaMalloc(&w.rw.counter, sizeof(int)));
-  CK(cudaMemset(w.rw.counter, 0, sizeof(int)));
+  CK(malloc_async(&w.rw.coop, (size_t)coop_blocks() * (MAXCOL + 1) * sizeof(df64), st));
+  CK(malloc_async(&w.rw.h, (MAXCOL + 1) * sizeof(df64), st));
+  CK(malloc_async(&w.rw.nrm, sizeof(df64), st));
+  CK(malloc_async(&w.rw.counter, sizeof(int), st));
+  CK(cudaMemsetAsync(w.rw.counter, 0, sizeof(int), st));
   const size_t sq = (size_t)cols * cols * sizeof(df64);
-  CK(cudaMalloc(&w.sw.A, sq));
-  CK(cudaMalloc(&w.sw.W, sq));
-  CK(cudaMalloc(&w.sw.P, sq));
-  CK(cudaMalloc(&w.sw.Q, sq));
-  CK(cudaMalloc(&w.sw.sigma, cols * sizeof(df64)));
-  CK(cudaMalloc(&w.sw.resid, cols * sizeof(double)));
-  CK(cudaMalloc(&w.sw.sigma_d, cols * sizeof(double)));
-  CK(cudaMalloc(&w.sw.conv, sizeof(int)));
-  CK(cudaMalloc(&w.est, sizeof(df64)));
-  CK(cudaMalloc(&w.dummy, sizeof(df64)));
-  CK(cudaMalloc(&w.flag, sizeof(int)));
-  CK(cudaMalloc(&w.status, sizeof(unsigned)));
+  CK(malloc_async(&w.sw.A, sq, st));
+  CK(malloc_async(&w.sw.W, sq, st));
+  CK(malloc_async(&w.sw.P, sq, st));
+  CK(malloc_async(&w.sw.Q, sq, st));
+  CK(malloc_async(&w.sw.sigma, cols * sizeof(df64), st));
+  CK(malloc_async(&w.sw.resid, cols * sizeof(double), st));
+  CK(malloc_async(&w.sw.sigma_d, cols * sizeof(double), st));
+  CK(malloc_async(&w.sw.conv, sizeof(int), st));
+  CK(malloc_async(&w.est, sizeof(df64), st));
+  CK(malloc_async(&w.dummy, sizeof(df64), st));
+  CK(malloc_async(&w.flag, sizeof(int), st));
+  CK(malloc_async(&w.status, sizeof(unsigned), st));
   w.rw.status = w.status;
-  CK(cudaMalloc(&w.sgn, cols * sizeof(int)));
+  CK(malloc_async(&w.sgn, cols * sizeof(int), st));
   w.dcap = d;
   return SSA_OK;
 }
@@ -622,11 +633,13 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   if (d > mn) d = (int)mn;
   if (d < k) d = k;
   REQ(d <= MAXCOL - 2, "Krylov dimension %d exceeds %d", d, MAXCOL - 2);
-  int kk = p->opts.keep > 0 ? p->opts.keep : k + (d - k + 1) / 2;
+  // keep k + ceil((d - k) / 5) Ritz pairs: fewer kept columns make the
+  // reorthogonalisation of each cycle cheaper and cost few extra restarts
+  int kk = p->opts.keep > 0 ? p->opts.keep : k + (d - k + 4) / 5;
   if (kk > d - 1) kk = d - 1;
   if (kk < k) kk = k;
   double tol = p->opts.tol;
-  if (!(tol > 0)) tol = prec == SSA_PREC_F32C ? 1e-7 * std::sqrt((double)ilog2(p->g.M)) : 1e-13;
+  if (!(tol > 0)) tol = prec == SSA_PREC_F32C ? 1e-7 * std::sqrt((double)ilog2(p->g.M)) : 1e-12;
   int rc = ensure_workspace(p, d);
   if (rc) return rc;
   Workspace& w = p->ws;
@@ -763,13 +776,13 @@ static int native_spectrum(ssa_plan_t p, Geom& g64) {
     for (int64_t m = 0; m < P; ++m) htw[m] = tw_entry64(m, P);
     for (int64_t m = 0; m < nA; ++m) hA[m] = tw_entry64(m << g.tws, M);
     for (int64_t m = 0; m < nB; ++m) hB[m] = tw_entry64(m, M);
-    CK(cudaMalloc(&p->tw64, P * sizeof(cplx<double>)));
-    CK(cudaMalloc(&p->tA64, nA * sizeof(cplx<double>)));
-    CK(cudaMalloc(&p->tB64, nB * sizeof(cplx<double>)));
-    CK(cudaMalloc(&p->chat64, (n + 1) * sizeof(cplx<double>)));
-    CK(cudaMemcpy(p->tw64, htw.data(), P * sizeof(cplx<double>), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(p->tA64, hA.data(), nA * sizeof(cplx<double>), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(p->tB64, hB.data(), nB * sizeof(cplx<double>), cudaMemcpyHostToDevice));
+    CK(malloc_async(&p->tw64, P * sizeof(cplx<double>), p->stream));
+    CK(malloc_async(&p->tA64, nA * sizeof(cplx<double>), p->stream));
+    CK(malloc_async(&p->tB64, nB * sizeof(cplx<double>), p->stream));
+    CK(malloc_async(&p->chat64, (n + 1) * sizeof(cplx<double>), p->stream));
+    CK(cudaMemcpyAsync(p->tw64, htw.data(), P * sizeof(cplx<double>), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->tA64, hA.data(), nA * sizeof(cplx<double>), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->tB64, hB.data(), nB * sizeof(cplx<double>), cudaMemcpyHostToDevice, p->stream));
   }
   g64 = g;
   g64.tw64 = p->tw64;
@@ -837,14 +850,40 @@ static int refine_sigma(ssa_plan_t p, ssa_decomp_s* res, int k) {
   return SSA_OK;
 }
 
+namespace ssa {
+int64_t plan_path_bytes(int64_t N, int64_t L, int k, int precision) {
+  const int64_t K = N - L + 1;
+  const int64_t Lw = L < K ? L : K, Kw = L < K ? K : L;
+  int64_t d = std::max<int64_t>(2 * k, k + 32);
+  d = std::min(d, Lw);
+  d = std::max<int64_t>(d, k);
+  const int64_t cols = d + 2;
+  int64_t M = 4;
+  while (M < N) M *= 2;
+  const int64_t n = M / 2;
+  const int64_t ldu = (Lw + 3) / 4 * 4, ldv = (Kw + 3) / 4 * 4;
+  int64_t b = 0;
+  b += 2 * (ldu + ldv) * cols * 8;                                       // two basis pairs
+  b += cols * cols * 8 * 5 + ((Kw + 3) / 4 * 4) * 8;                     // B, SVD work, y
+  b += (int64_t)reorth_blocks(Kw) * (MAXCOL + 1) * 8;                    // partial sums
+  b += (int64_t)fused_tiles(Kw) * (FUSED_MAXCOL + 1) * 8;
+  b += (int64_t)coop_blocks() * (MAXCOL + 1) * 8;
+  b += (2 * n + 3 * (n + 1)) * 16 + N * 8;                               // tables, spectrum, scratch, f
+  b += (L + K) * k * 16 + k * 16;                                        // results (double and df64)
+  (void)precision;
+  return b + (4 << 20);                                                  // allocator granularity
+}
+}  // namespace ssa
+
 extern "C" void ssa_decomp_destroy(ssa_decomp_t d) {
   if (!d) return;
-  cudaFree(d->sigma);
-  cudaFree(d->resid);
-  cudaFree(d->U);
-  cudaFree(d->V);
-  cudaFree(d->Uw);
-  cudaFree(d->Vw);
+  cudaStream_t st = d->plan ? d->plan->stream : nullptr;
+  free_async(d->sigma, st);
+  free_async(d->resid, st);
+  free_async(d->U, st);
+  free_async(d->V, st);
+  free_async(d->Uw, st);
+  free_async(d->Vw, st);
   delete d;
 }
 
@@ -870,12 +909,12 @@ extern "C" int ssa_decompose(ssa_plan_t p, const double* f, int k, ssa_decomp_t*
       return e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA; \
     }                                               \
   } while (0)
-  DK(cudaMalloc(&d->sigma, k * sizeof(double)));
-  DK(cudaMalloc(&d->resid, k * sizeof(double)));
-  DK(cudaMalloc(&d->U, (size_t)p->L * k * sizeof(double)));
-  DK(cudaMalloc(&d->V, (size_t)p->K * k * sizeof(double)));
-  DK(cudaMalloc(&d->Uw, (size_t)p->Lw * k * sizeof(df64)));
-  DK(cudaMalloc(&d->Vw, (size_t)p->Kw * k * sizeof(df64)));
+  DK(malloc_async(&d->sigma, k * sizeof(double), p->stream));
+  DK(malloc_async(&d->resid, k * sizeof(double), p->stream));
+  DK(malloc_async(&d->U, (size_t)p->L * k * sizeof(double), p->stream));
+  DK(malloc_async(&d->V, (size_t)p->K * k * sizeof(double), p->stream));
+  DK(malloc_async(&d->Uw, (size_t)p->Lw * k * sizeof(df64), p->stream));
+  DK(malloc_async(&d->Vw, (size_t)p->Kw * k * sizeof(df64), p->stream));
 #undef DK
   int rc = lanczos(p, k, d);
   if (rc != SSA_OK && rc != SSA_ENOCONV) {

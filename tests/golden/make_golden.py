@@ -9,6 +9,7 @@ element-wise checks.
 
   python tests/golden/make_golden.py many_sines_1M     # N = 2^20, L = 2^19, k = 50
   python tests/golden/make_golden.py realdata_shapes   # N = 5113 / 86867 stand-ins
+  python tests/golden/make_golden.py damped_4M         # N = 2^22, L = 2^21, k = 100 (precision stress)
 """
 import os
 import sys
@@ -67,6 +68,17 @@ def realdata_shapes():
         _write(f"sigma_three_sines_N{N}_L{L}_k{k}.txt",
                [f"series: synth.three_sines(N={N}, seed={seed}) (shape of the section 7 real-data runs)",
                 "tol 1e-14, seed 0"], f, L, k, out, time.time() - t)
+
+
+def damped_4M():
+    N, L, k = 1 << 22, 1 << 21, 100
+    f = synth.damped_sines(N, seed=3)
+    t = time.time()
+    out = ssa.decompose(f, L, k, method="lanczos", tol=1e-14, seed=0)
+    _write("sigma_damped_sines_N4194304_L2097152_k100.txt",
+           ["series: synth.damped_sines(N=2^22, seed=3): 20 damped cosines (rank 40, damping in",
+            "[0.9999, 1], periods log-uniform [5,5000], amplitude 1) + N(0, 1e-6^2)", "tol 1e-14, seed 0"],
+           f, L, k, out, time.time() - t)
 
 
 if __name__ == "__main__":
