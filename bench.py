@@ -43,6 +43,12 @@ WORKLOADS = {
     "many_sines_N512K": dict(N=1 << 19, L=1 << 18, k=50, gen="many_sines", seed=1, golden=None),
     # N = 1000 three-sine series (the paper-sized small case)
     "three_sines_N1000": dict(N=1000, L=500, k=10, gen="three_sines", seed=0, golden=None),
+    # 4096 ragged series in one persistent launch: N ~ U{500..20000}, L alternating round(N/3) and N//2,
+    # k ~ U{4..32}, three-sine generator with per-series seeds; FP32-compensated products
+    "batch_4096": dict(kind="batch", count=4096, seed=2),
+    # Poisson arrivals at 2000 requests/s into the request server: N log-uniform in [1e3, 1e6], L = N//2,
+    # k ~ U{2..64}, 40 GiB admission budget; each step is one arrival window of --window seconds
+    "serving_2000rps": dict(kind="serving", rate=2000.0, seed=4),
 }
 
 # ncu DRAM traffic per launch of the dominant kernel, keyed by kernel name;
@@ -211,6 +217,264 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------- many-series workloads
+def side_schedule(dimL, dimK, d, kk, restarts):
+    """(basis columns, vector length) of every reorthogonalisation of one
+    thick-restart Lanczos run, in the order the engine runs them."""
+    out = [(0, dimL), (0, dimK)]            # p_0 and the first v
+    r, c = 1, 1
+    for cyc in range(restarts + 1):
+        while c < d + 1:
+            out.append((r, dimL))
+            r += 1
+            out.append((c, dimK))
+            c += 1
+        if cyc < restarts:
+            r, c = kk, kk + 1
+    return out
+
+
+def lanczos_bytes(N, L, k, d, kk, restarts, M, s=8):
+    """Algorithmic bytes of one decomposition by the per-unit figures: each
+    product s(N + M) (input, output, half spectrum at 16 B per complex), each
+    CGS2 reorthogonalisation 3 passes over its basis plus the vector, each
+    restart the Ritz products."""
+    K = N - L + 1
+    Lw, Kw = min(L, K), max(L, K)
+    mv = s * (Lw + Kw) + 16 * (M // 2 + 1)
+    tot = 0.0
+    for ncols, dim in side_schedule(Lw, Kw, d, kk, restarts):
+        tot += mv + 8.0 * (3 * ncols * dim + 5 * dim)
+    tot += restarts * 8.0 * ((d + kk) * Lw + (d + kk) * Kw)
+    tot += 8.0 * ((d + k) * (Lw + Kw))
+    return tot
+
+
+def default_dims(L, K, k):
+    mn = min(L, K)
+    d = min(max(2 * k, k + 32), mn)
+    d = max(d, k)
+    kk = min(max(k + (d - k + 4) // 5, k), max(d - 1, k))
+    return d, kk
+
+
+def cpu_sample_series(specs, halfsteps=6, budget_s=20.0):
+    """Oracle Lanczos on a bounded sample of series, one process per core
+    (spawned before any GPU work in the pool): seconds per half-step each."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    cores = os.cpu_count() or 1
+    with ctx.Pool(min(cores, len(specs))) as pool:
+        t = time.perf_counter()
+        res = pool.map(_cpu_one, [(N, L, k, seed, halfsteps) for (N, L, k, seed) in specs])
+        wall = time.perf_counter() - t
+    return res, wall, min(cores, len(specs))
+
+
+def _cpu_one(a):
+    N, L, k, seed, halfsteps = a
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    from oracle import ssa as ossa
+    from paper_0911_4498_gb300 import synth
+    f = synth.three_sines(N, seed=seed)
+    t = time.perf_counter()
+    out = ossa.decompose(f, L, k, method="lanczos", max_steps=halfsteps)
+    return (time.perf_counter() - t) / max(1, int(out.get("steps", halfsteps)))
+
+
+def run_gpu_batch(args, w):
+    import torch
+    from paper_0911_4498_gb300 import build, synth
+    build.build()
+    import paper_0911_4498_gb300 as ssa
+    series_l, Ls, ks = synth.batch_workload(w["count"], seed=w["seed"])
+    n = len(series_l)
+    Ns = np.array([f.size for f in series_l], dtype=np.int64)
+    off = np.zeros(n + 1, dtype=np.int64)
+    off[1:] = np.cumsum(Ns)
+    f_host = np.concatenate(series_l)
+    Ls = Ls.astype(np.int64)
+    ks32 = ks.astype(np.int32)
+    prec = ssa.SSA_PREC_F32C if args.precision_batch == "f32c" else ssa.SSA_PREC_F64
+    stream = torch.cuda.current_stream()
+    opts = ssa.make_opts(precision=prec, stream=stream.cuda_stream)
+    f_dev = torch.from_numpy(f_host).cuda()
+    off_d = torch.from_numpy(off).cuda()
+    L_d = torch.from_numpy(Ls).cuda()
+    k_d = torch.from_numpy(ks32).cuda()
+    sig_all = np.empty(int(ks.sum()))
+
+    def step(fin, offs, Lsx, ksx, collect=False):
+        b, rc = ssa.ssa_decompose_batch(fin, offs, Lsx, ksx, opts)
+        infos = None
+        try:
+            if collect:
+                infos = [ssa.ssa_batch_info(b, i) for i in range(n)]
+                pos = 0
+                for i in range(n):
+                    ssa.ssa_batch_get(b, i, sig_all[pos:pos + ks[i]])
+                    pos += ks[i]
+        finally:
+            ssa.ssa_batch_destroy(b)
+        return rc, infos
+
+    rc, infos = step(f_dev, off_d, L_d, k_d, collect=True)
+    for _ in range(max(0, args.warmup - 1)):
+        step(f_dev, off_d, L_d, k_d)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = ssa.ssa_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(f_dev, off_d, L_d, k_d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = sampler.stop()
+    launches = ssa.ssa_kernel_launches() - launches0
+    value = n / (ms / 1000.0)
+    # end to end with host arrays: H2D of all series inside the call, D2H of every sigma
+    f_pin = torch.from_numpy(f_host).pin_memory()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        b, _ = ssa.ssa_decompose_batch(f_pin.numpy(), off, Ls, ks32, opts)
+        pos = 0
+        for i in range(n):
+            ssa.ssa_batch_get(b, i, sig_all[pos:pos + ks[i]])
+            pos += ks[i]
+        ssa.ssa_batch_destroy(b)
+    e2e_dt = (time.perf_counter() - t) / args.steps
+    # accuracy on a sample of series against the oracle
+    from oracle import ssa as ossa
+    sample = list(range(0, n, max(1, n // 6)))[:6]
+    errs = []
+    starts = np.concatenate([[0], np.cumsum(ks)])
+    for i in sample:
+        ref = ossa.decompose(series_l[i], int(Ls[i]), int(ks[i]), method="jacobi" if Ns[i] <= 1500 else "lanczos")
+        got = sig_all[starts[i]:starts[i + 1]]
+        errs.append(float(np.max(np.abs(got - ref["sigma"]) / ref["sigma"])))
+    # algorithmic bytes of the launch by the per-unit figures and the engine's restart schedule
+    tot_bytes = 0.0
+    for i in range(n):
+        K = int(Ns[i] - Ls[i] + 1)
+        d, kk = default_dims(int(Ls[i]), K, int(ks[i]))
+        M = 4
+        while M < Ns[i]:
+            M *= 2
+        tot_bytes += lanczos_bytes(int(Ns[i]), int(Ls[i]), int(ks[i]), d, kk, infos[i]["restarts"], M,
+                                   s=4 if prec == ssa.SSA_PREC_F32C else 8)
+    hbm, peak_kind = peaks()
+    achieved = tot_bytes / (ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": "k_batch_ssa", "bytes_per_launch": tot_bytes, "ms_per_launch": ms,
+            "launches": args.steps, "peak_source": peak_kind,
+            "note": "algorithmic bytes of all series by the per-unit formulas; most of each series' working "
+                    "set stays in L2 and shared memory, so HBM does not bound this kernel"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        pick = list(range(0, n, max(1, n // 32)))[:32]
+        per_half, wall, cores = cpu_sample_series([(int(Ns[i]), int(Ls[i]), int(ks[i]), 2 * 1_000_003 + i)
+                                                   for i in pick], args.sample_halfsteps)
+        est = [per_half[j] * infos[i]["matvecs"] for j, i in enumerate(pick)]
+        cpu = {"value": (os.cpu_count() or 1) / statistics.mean(est), "unit": UNIT, "cores": os.cpu_count() or 1,
+               "kind": "oracle",
+               "sample": f"oracle Lanczos, first {args.sample_halfsteps} half-steps of {len(pick)} of the series "
+                         f"(one per core, {wall:.1f} s), scaled to each series' half-step count on the GPU; all "
+                         "cores busy"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+df64" if prec == ssa.SSA_PREC_F32C else "df64", "data": "synthetic",
+            "config": {"workload": args.workload, "series": n, "N": "U{500..20000}", "L": "round(N/3) | N//2",
+                       "k": "U{4..32}", "total_samples": int(Ns.sum()), "precision": args.precision_batch,
+                       "l2": "inputs 0.33 GB, larger than L2; no flush"},
+            "sigma_rel_err_max_sample": max(errs), "converged": all(i["converged"] for i in infos),
+            "matvecs_mean": float(np.mean([i["matvecs"] for i in infos])), "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": n / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(8 * Ns.sum()),
+                    "d2h_bytes_per_step": int(8 * ks.sum())},
+            "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu_serving(args, w):
+    import torch
+    from paper_0911_4498_gb300 import build, synth
+    build.build()
+    import paper_0911_4498_gb300 as ssa
+    prec = ssa.SSA_PREC_F32C if args.precision_batch == "f32c" else ssa.SSA_PREC_F64
+    def window(i):
+        arr = synth.serving_arrivals(w["rate"], args.window, seed=w["seed"] + i)
+        return [(t, N, L, k, synth.three_sines(N, seed=sd)) for (t, N, L, k, sd) in arr]
+
+    srv = ssa.ssa_serve_create(ssa.make_serve_opts(precision=prec))
+    sampler = None
+    lat, done_n, t_total, nreq, batched = [], 0, 0.0, 0, 0
+    launches0 = None
+    try:
+        for wi in range(args.warmup + args.steps):
+            reqs = window(wi)
+            timed = wi >= args.warmup
+            if timed and sampler is None:
+                torch.cuda.synchronize()
+                sampler = ClockSampler(0)
+                sampler.start()
+                launches0 = ssa.ssa_kernel_launches()
+            t0 = time.perf_counter()
+            ids = []
+            for (ta, N, L, k, f) in reqs:
+                now = time.perf_counter() - t0
+                if ta > now:
+                    time.sleep(ta - now)
+                ids.append((ssa.ssa_serve_submit(srv, f, L, k, 0), k, time.perf_counter()))
+            for rid, k, ts in ids:
+                while not ssa.ssa_serve_poll(srv, rid, 1.0):
+                    pass
+                rc, info = ssa.ssa_serve_take(srv, rid, np.empty(k))
+                if timed:
+                    lat.append(info["t_done"] - info["t_submit"])
+                    batched += info["batched"]
+            t_end = time.perf_counter()
+            if timed:
+                t_total += t_end - t0
+                nreq += len(ids)
+        stats = ssa.ssa_serve_stats(srv)
+    finally:
+        ssa.ssa_serve_destroy(srv)
+    clocks = sampler.stop()
+    launches = ssa.ssa_kernel_launches() - launches0
+    value = nreq / t_total
+    # sequential plain FP64 single-series path on the first requests of the first timed window
+    seq = window(args.warmup)[:args.seq_sample]
+    t = time.perf_counter()
+    for (_, N, L, k, f) in seq:
+        plan = ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=ssa.SSA_PREC_F64))
+        d, _ = ssa.ssa_decompose(plan, f, k)
+        sg = np.empty(k)
+        ssa.ssa_decomp_get(d, sg, None, None, None)
+        ssa.ssa_decomp_destroy(d)
+        ssa.ssa_plan_destroy(plan)
+    seq_rate = len(seq) / (time.perf_counter() - t)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64" if prec == ssa.SSA_PREC_F32C else "df64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "arrival_rate": w["rate"], "window_s": args.window,
+                       "N": "log-uniform [1e3, 1e6]", "L": "N//2", "k": "U{2..64}", "mem_budget_GiB": 40,
+                       "precision": args.precision_batch, "outputs": "sigma and residuals"},
+            "requests": nreq, "batched_requests": batched,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "offered_rps": w["rate"], "sequential_f64": {"value": seq_rate, "requests": len(seq)},
+            "speedup_vs_sequential_f64": value / seq_rate, "mem_peak_GiB": stats["mem_peak"] / 2**30,
+            "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+            "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -227,6 +491,10 @@ def run_gpu(args):
     import paper_0911_4498_gb300 as ssa
 
     w = WORKLOADS[args.workload]
+    if w.get("kind") == "batch":
+        return run_gpu_batch(args, w)
+    if w.get("kind") == "serving":
+        return run_gpu_serving(args, w)
     N, L, k = w["N"], w["L"], w["k"]
     K = N - L + 1
     prec = ssa.SSA_PREC_F32C if args.precision == "f32c" else ssa.SSA_PREC_F64
@@ -394,6 +662,10 @@ def main():
     ap.add_argument("--sample-halfsteps", type=int, default=6)
     ap.add_argument("--ref-halfsteps-full", type=int, default=400)
     ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--precision-batch", default="f32c", choices=["f64", "f32c"],
+                    help="precision of the batch and serving workloads")
+    ap.add_argument("--window", type=float, default=0.25, help="serving: arrival window per step (s)")
+    ap.add_argument("--seq-sample", type=int, default=40, help="serving: requests timed sequentially in FP64")
     args = ap.parse_args()
     if args.cpu_worker:
         cpu_worker(args)
