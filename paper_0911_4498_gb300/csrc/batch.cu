@@ -350,12 +350,21 @@ SSA_D void cta_cgs_pass(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t 
 }
 
 // w <- (I - Q Q^T)^2 w; returns w.w (valid in all threads)
+// mode: REORTH_ONCE (FP32 products) or REORTH_GATED (the third pass only
+// when ||w'||^2 < ||w||^2 / 2 after the first update, Kahan-Parlett).
 SSA_D df64 cta_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, df64* h1, df64* h2, df64* scal_,
-                    df64* stbuf) {
+                    df64* stbuf, int mode) {
   if (ncols > 0) {
     cta_cgs_pass<false, true>(Q, ldq, ncols, w, dim, nullptr, h1, nullptr, stbuf);
-    cta_cgs_pass<true, true>(Q, ldq, ncols, w, dim, h1, h2, nullptr, stbuf);
-    cta_cgs_pass<true, false>(Q, ldq, ncols, w, dim, h2, nullptr, scal_, stbuf);
+    __syncthreads();
+    if (mode == REORTH_GATED) {
+      cta_cgs_pass<true, true>(Q, ldq, ncols, w, dim, h1, h2, nullptr, stbuf);
+      __syncthreads();
+      if (!df_lt(df_scale(h2[ncols], 2.0f), h1[ncols])) return h2[ncols];
+      cta_cgs_pass<true, false>(Q, ldq, ncols, w, dim, h2, nullptr, scal_, stbuf);
+    } else {
+      cta_cgs_pass<true, false>(Q, ldq, ncols, w, dim, h1, nullptr, scal_, stbuf);
+    }
   } else {
     cta_cgs_pass<true, false>(Q, ldq, 0, w, dim, h1, nullptr, scal_, stbuf);
   }
@@ -432,6 +441,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
     const int64_t Lw = S.Lw, Kw = S.Kw, ldu = cx.ldu, ldv = cx.ldv;
     const int ldb = B_MAXC;
     const uint64_t seed = cx.seed;  // same draws alone and in any batch
+    const int reorth = cx.precision == SSA_PREC_F32C ? REORTH_ONCE : REORTH_GATED;
     // spectrum
     cta_spectrum(g, f, sl.chat, sl.fscr, dbuf);
     // clear the projected matrix; state
@@ -464,7 +474,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
       } else {
         for (int64_t i = threadIdx.x; i < dim; i += BT) w[i] = sm64_uniform_pm1(seed, stream_id, i);
         __syncthreads();
-        const df64 n2 = cta_cgs2(Qb, ldq, ncols, w, dim, h1, h2, &sc_nrm, stbuf);
+        const df64 n2 = cta_cgs2(Qb, ldq, ncols, w, dim, h1, h2, &sc_nrm, stbuf, reorth);
         const df64 nb = df_sqrt(n2);
         const bool alive = ncols < dim && nb.hi > 1e-6f * sqrtf((float)dim / 3.f);
         const df64 inv = alive ? df_div(make_df(1.f, 0.f), nb) : df_zero();
@@ -482,7 +492,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
     ++stream_id;
     __syncthreads();
     {
-      const df64 n2 = cta_cgs2(U, ldu, 0, sl.y, Lw, h1, h2, &sc_nrm, stbuf);
+      const df64 n2 = cta_cgs2(U, ldu, 0, sl.y, Lw, h1, h2, &sc_nrm, stbuf, reorth);
       normalize(sl.y, Lw, n2, U, ldu, 0, &sl.T[0]);
     }
     int r = 1, c = 0;
@@ -495,7 +505,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
       df64* bentry = vside ? sl.B + (int64_t)(r - 1) * ldb + c : sl.B + (int64_t)r * ldb + (c - 1);
       cta_matvec<T, MAXE>(g, vside ? 1 : 0, src, sl.y, sl.chat, fbuf);
       ++matvecs;
-      const df64 n2 = cta_cgs2(Qb, ldq, ncols, sl.y, dim, h1, h2, &sc_nrm, stbuf);
+      const df64 n2 = cta_cgs2(Qb, ldq, ncols, sl.y, dim, h1, h2, &sc_nrm, stbuf, reorth);
       normalize(sl.y, dim, n2, Qb, ldq, ncols, bentry);
       ++stream_id;
       if (vside) ++c;

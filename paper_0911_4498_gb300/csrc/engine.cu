@@ -202,6 +202,8 @@ struct Workspace {
     free_async(rw.part2, st);
     free_async(rw.coop, st);
     free_async(rw.h, st);
+    free_async(rw.h2, st);
+    free_async(rw.gate, st);
     free_async(rw.nrm, st);
     free_async(rw.counter, st);
     free_async(sw.A, st);
@@ -601,6 +603,8 @@ static int ensure_workspace(ssa_plan_t p, int d) {
   reorth_setup();
   CK(malloc_async(&w.rw.coop, (size_t)coop_blocks() * (MAXCOL + 1) * sizeof(df64), st));
   CK(malloc_async(&w.rw.h, (MAXCOL + 1) * sizeof(df64), st));
+  CK(malloc_async(&w.rw.h2, (MAXCOL + 1) * sizeof(df64), st));
+  CK(malloc_async(&w.rw.gate, sizeof(int), st));
   CK(malloc_async(&w.rw.nrm, sizeof(df64), st));
   CK(malloc_async(&w.rw.counter, sizeof(int), st));
   CK(cudaMemsetAsync(w.rw.counter, 0, sizeof(int), st));
@@ -658,7 +662,10 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   int64_t matvecs = 0;
   // p_0 (Algorithm 1, line 1): seeded uniform(-1, 1), normalised into u_1
   launch_random_fill(w.y, Lw, seed, stream_id++, s);
-  launch_cgs2(U, w.ldu, 0, w.y, Lw, w.rw, nullptr, s);
+  // one reorthogonalisation pass suffices when the products are FP32 (their
+  // error, ~1e-7 sigma_1, is far above one pass's df64 orthogonality)
+  const int reorth = prec == SSA_PREC_F32C ? REORTH_ONCE : REORTH_GATED;
+  launch_cgs2(U, w.ldu, 0, w.y, Lw, w.rw, reorth, s);
   CK((cudaError_t)launch_normalize_coop(w.y, Lw, w.rw, U, w.dummy, w.est, U, w.ldu, 0, seed, stream_id++, w.status,
                                         s));
   CHECK_LAUNCH();
@@ -673,7 +680,7 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     df64* bentry = vside ? w.B + (int64_t)(r - 1) * w.ldb + c : w.B + (int64_t)r * w.ldb + (c - 1);
     launch_matvec_df(p->g, prec, vside ? 1 : 0, src, 0, w.y, 0, 1, p->chat, p->scratch, s);
     ++matvecs;
-    launch_cgs2(Qb, ldq, ncols, w.y, dim, w.rw, nullptr, s);
+    launch_cgs2(Qb, ldq, ncols, w.y, dim, w.rw, reorth, s);
     df64* qcol = Qb + (int64_t)ncols * ldq;
     CK((cudaError_t)launch_normalize_coop(w.y, dim, w.rw, qcol, bentry, w.est, Qb, ldq, ncols, seed, stream_id,
                                           w.status, s));

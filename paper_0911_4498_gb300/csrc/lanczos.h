@@ -18,7 +18,9 @@ struct ReorthWork {
   df64* part2;   // [tiles][ldp] partial sums of the fused pass (tiles of 64 rows)
   int ldp;
   int ldp2;      // leading dimension of part2 (FUSED_MAXCOL + 1)
-  df64* h;       // projection coefficients (MAXCOL + 1)
+  df64* h;       // projection coefficients of the first pass; h[ncols] = ||w||^2 (MAXCOL + 1)
+  df64* h2;      // the same for the second pass; h2[ncols] = ||w'||^2 (MAXCOL + 1)
+  int* gate;     // 1 when the third pass must run (Kahan-Parlett test on the device)
   df64* nrm;     // squared norm after the last update
   int* counter;  // last-block counter (returns to 0 after each kernel)
   df64* coop;    // [coop_blocks()][MAXCOL + 1] scratch of the breakdown branch
@@ -37,7 +39,14 @@ struct SvdWork {
 int reorth_blocks(int64_t dim);
 int fused_tiles(int64_t dim);
 void reorth_setup();
-void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, const int* flag,
+// Classical Gram-Schmidt of w against the ncols columns of Q, then
+// nrm2 <- ||w||^2.  REORTH_ONCE: one projection and update (two passes over
+// Q).  REORTH_GATED: a second projection; its update (a third pass) runs only
+// when ||w'||^2 < ||w||^2 / 2 after the first (Kahan-Parlett), so the result
+// is orthogonal to Q to working precision either way.  Bases wider than
+// FUSED_MAXCOL always take both passes.
+enum { REORTH_ONCE = 1, REORTH_GATED = 2 };
+void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, int mode,
                  cudaStream_t s);
 void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est, int* flag, int mode,
                       uint64_t seed, uint64_t stream, unsigned* status, cudaStream_t s);

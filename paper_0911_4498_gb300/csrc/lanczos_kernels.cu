@@ -97,6 +97,28 @@ __global__ void k_reduce_cols(const df64* __restrict__ part, int ntiles, int ldp
   if (lane == 0) out[col] = s;
 }
 
+// Second-pass reduction: out[i] for i <= ncols (out[ncols] = ||w'||^2), and
+// the Kahan-Parlett decision for the third pass: *gate = ||w'||^2 < ref/2
+// with ref = ||w||^2 before the first update; without a third pass
+// ||w'||^2 is the final squared norm.
+__global__ void k_reduce_gate(const df64* __restrict__ part, int ntiles, int ldp, int ncols, df64* __restrict__ out,
+                              const df64* __restrict__ ref, int* __restrict__ gate, df64* __restrict__ nrm) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col > ncols) return;
+  df64 s = df_zero();
+  for (int t = lane; t < ntiles; t += 32) s = df_add(s, part[(int64_t)t * ldp + col]);
+  s = warp_sum_df(s);
+  if (lane == 0) {
+    out[col] = s;
+    if (col == ncols) {
+      const bool again = df_lt(df_scale(s, 2.0f), *ref);
+      *gate = again ? 1 : 0;
+      if (!again) *nrm = s;
+    }
+  }
+}
+
 // Tile-walking CGS pass over Q (dim x ncols, ncols <= FUSED_MAXCOL):
 //   UPD:  w <- w - Q h          (h read from memory)
 //   PROJ: part[block][c] = sum over the block's tiles of Q[tile, c] . w[tile]
@@ -627,61 +649,69 @@ int reorth_blocks(int64_t dim) { return (int)((dim + SLAB - 1) / SLAB); }
 int fused_tiles(int64_t dim) { return (int)((dim + FR - 1) / FR); }
 int fused_grid(size_t smem_bytes);
 
-// CGS2: w <- (I - Q Q^T)^2 w, nrm2 <- ||w||^2.  flag (may be null) gates the
-// whole sequence on the device (used for the breakdown replacement).
-void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, const int* flag,
+void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, int mode,
                  cudaStream_t s) {
   const int G = reorth_blocks(dim);
   // algorithmic bytes: the ncols basis columns once per pass, w read (and written by updates)
   const double qb = 8.0 * (double)dim * ncols;
   const double fl = 2.0 * (double)dim * ncols;
-  const int gated = flag ? 1 : 0;
+  const int* flag = nullptr;
   if (ncols <= FUSED_MAXCOL) {
     const int T2 = fused_tiles(dim);
     const size_t sm = ((size_t)NST * (ncols * FRP + FR) + ncols) * sizeof(df64);
     const int G2 = T2 < fused_grid(sm) ? T2 : fused_grid(sm);
     const int ldp = rw.ldp2;
+    const df64* hlast = rw.h;
+    const int* gate = nullptr;
     if (ncols > 0) {
+      // pass 1: h = Q^T w and ||w||^2 (column ncols)
       prof_begin(s);
       k_cgs_tiles<false, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag, rw.status);
-      prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
+      prof_end(s, K_PROJ, qb + 8.0 * dim, fl);
       prof_begin(s);
-      k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols, rw.h, flag);
-      prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
-      prof_begin(s);
-      k_cgs_tiles<true, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag, rw.status);
-      prof_end(s, gated ? K_GATED : K_UPDATE_PROJ, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : 2 * fl);
-      prof_begin(s);
-      k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols, rw.h, flag);
-      prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+      k_reduce_cols<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols + 1, rw.h, flag);
+      prof_end(s, K_MISC, 0.0, 0.0);
+      if (mode == REORTH_GATED) {
+        // pass 2: w <- w - Q h, h2 = Q^T w, ||w||^2; the gate decides on pass 3
+        prof_begin(s);
+        k_cgs_tiles<true, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag, rw.status);
+        prof_end(s, K_UPDATE_PROJ, qb + 16.0 * dim, 2 * fl);
+        prof_begin(s);
+        k_reduce_gate<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols, rw.h2, rw.h + ncols, rw.gate,
+                                                      rw.nrm);
+        prof_end(s, K_MISC, 0.0, 0.0);
+        hlast = rw.h2;
+        gate = rw.gate;
+      }
     }
+    // last pass: w <- w - Q h, ||w||^2 (skipped on the device when the gate is 0)
     prof_begin(s);
-    k_cgs_tiles<true, false><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag, rw.status);
-    prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
+    k_cgs_tiles<true, false><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, hlast, rw.part2, ldp, T2, gate, rw.status);
+    prof_end(s, gate ? K_GATED : K_UPDATE, gate ? 0.0 : qb + 16.0 * dim, gate ? 0.0 : fl);
     prof_begin(s);
-    k_reduce_one<<<1, 32, 0, s>>>(rw.part2, G2, ldp, ncols, rw.nrm, flag);
-    prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+    k_reduce_one<<<1, 32, 0, s>>>(rw.part2, G2, ldp, ncols, rw.nrm, gate);
+    prof_end(s, K_MISC, 0.0, 0.0);
     return;
   }
   // wide bases: batched passes (four reads of Q)
   prof_begin(s);
   k_cgs_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, flag);
-  prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
+  prof_end(s, K_PROJ, qb + 8.0 * dim, fl);
   prof_begin(s);
   k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part, G, rw.ldp, ncols, rw.h, flag);
-  prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+  prof_end(s, K_MISC, 0.0, 0.0);
   prof_begin(s);
   k_cgs_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
-  prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
+  prof_end(s, K_UPDATE, qb + 16.0 * dim, fl);
   prof_begin(s);
   k_cgs_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, flag);
-  prof_end(s, gated ? K_GATED : K_PROJ, gated ? 0.0 : qb + 8.0 * dim, gated ? 0.0 : fl);
+  prof_end(s, K_PROJ, qb + 8.0 * dim, fl);
   prof_begin(s);
   k_reduce_cols<<<(ncols + 7) / 8, 256, 0, s>>>(rw.part, G, rw.ldp, ncols, rw.h, flag);
-  prof_end(s, gated ? K_GATED : K_MISC, 0.0, 0.0);
+  prof_end(s, K_MISC, 0.0, 0.0);
   prof_begin(s);
   k_cgs_update<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part, rw.nrm, rw.counter, flag);
-  prof_end(s, gated ? K_GATED : K_UPDATE, gated ? 0.0 : qb + 16.0 * dim, gated ? 0.0 : fl);
+  prof_end(s, K_UPDATE, qb + 16.0 * dim, fl);
 }
 
 static int g_sms = 0;
