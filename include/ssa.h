@@ -188,7 +188,41 @@ int ssa_batch_info(ssa_batch_t b, int i, int* k, int* converged, int* restarts, 
 /* Results of series i: sigma (k), U (L x k), V (K x k), resid (k); NULL skips an output. */
 int ssa_batch_get(ssa_batch_t b, int i, double* sigma, double* U, double* V, double* resid);
 
+/*
+ * Grouped Hankelization (Algorithm 4 summed over each group, divided by the
+ * antidiagonal counts of section 5) of every series of a batch, with the
+ * same groups for all series: CSR groups as in ssa_reconstruct, indices
+ * below every series' k.  out: for series i, an m x N_i row-major block,
+ * blocks in series order (sum_i m N_i doubles, host or device).
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA.
+ */
+int ssa_batch_reconstruct(ssa_batch_t b, const int32_t* grp_off, const int32_t* grp_idx, int m, double* out);
+
 void ssa_batch_destroy(ssa_batch_t b);
+
+/* ---- heterogeneity matrix (section 6.4) -------------------------------- */
+
+/*
+ * H-matrix G_{B,T}: g_ij = g(base_i, test_j) for the base subseries
+ * base_i = (f_i, ..., f_{i+B-1}), i = 0..N-B, and the test subseries
+ * test_j = (f_j, ..., f_{j+T-1}), j = 0..N-T, where g(F1, F2) is the
+ * heterogeneity index (eq. g): the share of the squared norm of F2's
+ * L-lagged vectors that lies outside the span of F1's left singular vectors
+ * U_l, l in I.  (The paper prints F_{i,i+B}; the base holds B samples.)
+ *   f:    N doubles (host or device)
+ *   I:    nI distinct 1-based triple indices (host), each <= min(L, B-L+1)
+ *   opts: precision, tolerance and stream of the base decompositions and products
+ *   H:    (N-B+1) x (N-T+1) doubles, row-major (host or device), caller-owned
+ * The base decompositions run as batched launches over the sliding windows
+ * (one plan reused per window where B exceeds the batched engine's limits);
+ * one Algorithm 3 product of the whole series per (base, l in I) gives
+ * U_l^T X_t for every lagged vector X_t, and windowed sums of their squares
+ * give every g_ij.  A test window that is identically zero gets g = 0.
+ * Errors: SSA_EINVAL (need 1 < L < B <= N, L <= T <= N), SSA_ENOMEM,
+ * SSA_ENOCONV (H is still written), SSA_ECUDA.
+ */
+int ssa_hmatrix(const double* f, int64_t N, int64_t L, int64_t B, int64_t T, const int32_t* I, int nI,
+                const ssa_opts_t* opts, double* H);
 
 /* ---- request server (continuous batching; not a step of the paper) ------ */
 

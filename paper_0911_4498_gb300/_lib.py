@@ -80,7 +80,9 @@ _SIGS = {
     "ssa_batch_info": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_I64)]),
     "ssa_batch_get": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "ssa_batch_reconstruct": (_I, [_VP, _VP, _VP, _I, _VP]),
     "ssa_batch_destroy": (None, [_VP]),
+    "ssa_hmatrix": (_I, [_VP, _I64, _I64, _I64, _I64, _VP, _I, ctypes.POINTER(SsaOpts), _VP]),
     "ssa_serve_default_opts": (None, [ctypes.POINTER(ServeOpts)]),
     "ssa_serve_create": (_I, [ctypes.POINTER(ServeOpts), ctypes.POINTER(_VP)]),
     "ssa_serve_submit": (_I, [_VP, _VP, _I64, _I64, _I, _I, ctypes.POINTER(_I64)]),
@@ -241,8 +243,27 @@ def ssa_batch_get(b, i: int, sigma=None, U=None, V=None, resid=None):
     _check(lib().ssa_batch_get(b, i, _ptr(sigma), _ptr(U), _ptr(V), _ptr(resid)))
 
 
+def ssa_batch_reconstruct(b, grp_off, grp_idx, m: int, out):
+    _check(lib().ssa_batch_reconstruct(b, _ptr(grp_off, np.int32), _ptr(grp_idx, np.int32), m, _ptr(out)))
+
+
 def ssa_batch_destroy(b):
     lib().ssa_batch_destroy(b)
+
+
+def ssa_hmatrix(f, L: int, B: int, T: int, I, opts: SsaOpts | None = None, out=None):
+    """H-matrix of section 6.4 (rows: base starts 0..N-B, columns: test starts 0..N-T).
+
+    f: float64 numpy array or CUDA tensor; I: 1-based triple indices.  Returns
+    (H, status) with status SSA_OK or SSA_ENOCONV."""
+    N = int(f.numel() if hasattr(f, "numel") else f.size)
+    idx = np.ascontiguousarray(np.asarray(I, dtype=np.int32))
+    if out is None:
+        out = np.empty((N - B + 1, N - T + 1))
+    rc = _check(lib().ssa_hmatrix(_ptr(f), N, L, B, T, idx.ctypes.data, len(idx),
+                                  ctypes.byref(opts) if opts is not None else None, _ptr(out)),
+                allow=(SSA_ENOCONV,))
+    return out, rc
 
 
 def ssa_serve_default_opts() -> ServeOpts:

@@ -523,11 +523,12 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
       const bool pre = cp >= 16 && ((size_t)r * cp + (size_t)cp * cp) * 4 <= (size_t)B_SMEM;
       if (pre) {
         float* A32 = reinterpret_cast<float*>(smem_raw);
-        svd_precondition_body<BT>(sl.B, ldb, r, cp, sl.A, sl.W, sl.T, cc, 40, 2e-6f, A32, A32 + r * cp);
+        svd_precondition_body<BT>(sl.B, ldb, r, cp, sl.A, sl.W, sl.T, cc, PRE_SWEEPS, 2e-6f, A32, A32 + r * cp);
         __syncthreads();
       }
+      // the FFT buffer is idle during the projected SVD: stage A and W there
       svd_jacobi_body<BT>(sl.B, ldb, r, cp, sl.A, sl.W, cc, sl.sigma, sl.P, sl.Q, sl.resid, sl.sigma_d, k, cx.tol,
-                          &conv, &est, &status, 60, 1e-13f, pre ? 1 : 0);
+                          &conv, &est, &status, 60, 1e-13f, pre ? 1 : 0, reinterpret_cast<df64*>(smem_raw));
       __syncthreads();
       const int converged = conv;
       __syncthreads();
@@ -769,6 +770,131 @@ __global__ void __launch_bounds__(BT) k_batch_refine(BCtx cx, BRefine rf) {
   }
 }
 
+// ---------------------------------------------------------------- grouped Hankelization
+// For every (series, group): g = irFFT(sum_{j in group} sigma_j rFFT(u'_j) . rFFT(v'_j)) / counts
+// (Algorithm 4 summed over the group, with the division by the antidiagonal
+// counts of section 5).  One persistent CTA per item at a time; the u'
+// spectrum and the group's accumulator (df64) live in the CTA's global
+// scratch, the FFTs in shared memory.
+struct BHCtx {
+  const BSeries* ser;
+  int nseries, m;
+  const double *U, *V, *sigma;
+  const int *grp_off, *grp_idx;
+  double* out;
+  const int64_t* out_off;  // per series: start of its m x N block in out
+  const cplx<df64>* tw;
+  int lg_P;
+  const cplx<df64>* tA;
+  const cplx<df64>* tB;
+  int tws, lg_Mmax;
+  cplx<df64>* scratch;
+  int64_t ld_scr;  // 2 (nmax + 1) per CTA
+  int* next;
+};
+
+template <class T, int MAXE>
+SSA_D void cta_rfft_pad(const Geom& g, const double* x, int64_t len, cplx<T>* buf) {
+  const int n = 1 << g.lg_n;
+  for (int t = threadIdx.x; t < n; t += BT) {
+    const int64_t j = 2 * (int64_t)t;
+    buf[t] = mk(j < len ? scal<T>::from_double(x[j]) : scal<T>::zero(),
+                j + 1 < len ? scal<T>::from_double(x[j + 1]) : scal<T>::zero());
+  }
+  __syncthreads();
+  cta_fft<T, BT, MAXE, false>(buf, g.lg_n, 1, g.tw, g.lg_P);
+}
+
+template <class T, int MAXE>
+__global__ void __launch_bounds__(BT, 1) k_batch_hankel(BHCtx cx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  __shared__ int s_item;
+  cplx<df64>* su = cx.scratch + (int64_t)blockIdx.x * cx.ld_scr;
+  cplx<df64>* acc = su + cx.ld_scr / 2;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(cx.next, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= cx.nseries * cx.m) break;
+    const int si = item / cx.m, grp = item - si * cx.m;
+    const BSeries S = cx.ser[si];
+    Geom g{};
+    g.N = S.N;
+    g.L = S.L;
+    g.K = S.K;
+    g.M = (int64_t)2 << S.lg_n;
+    g.lg_n = S.lg_n;
+    g.tw = cx.tw;
+    g.lg_P = cx.lg_P;
+    g.tA = cx.tA;
+    g.tB = cx.tB;
+    g.tws = cx.tws;
+    g.twshift = cx.lg_Mmax - (S.lg_n + 1);
+    const int n = 1 << g.lg_n;
+    for (int k = threadIdx.x; k <= n; k += BT) acc[k] = mk(df_zero(), df_zero());
+    for (int ii = cx.grp_off[grp]; ii < cx.grp_off[grp + 1]; ++ii) {
+      const int j = cx.grp_idx[ii];
+      const double* u = cx.U + S.out_u + (int64_t)j * S.L;
+      const double* v = cx.V + S.out_v + (int64_t)j * S.K;
+      const df64 sg = df_from_double(cx.sigma[S.out_s + j]);
+      cta_rfft_pad<T, MAXE>(g, u, S.L, buf);
+      for (int k = threadIdx.x; k <= n / 2; k += BT) {
+        const int nk = (n - k) & (n - 1);
+        const cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)k << g.twshift)
+                             : mk(scal<T>::from_double(1.0), scal<T>::zero());
+        cplx<T> wk, wnk;
+        rfft_post(buf[k], buf[nk], tw, wk, wnk);
+        su[k] = mk(scal<T>::to_df(wk.re), scal<T>::to_df(wk.im));
+        su[n - k] = mk(scal<T>::to_df(wnk.re), scal<T>::to_df(wnk.im));
+      }
+      __syncthreads();
+      cta_rfft_pad<T, MAXE>(g, v, S.K, buf);
+      for (int k = threadIdx.x; k <= n / 2; k += BT) {
+        const int nk = (n - k) & (n - 1);
+        const cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)k << g.twshift)
+                             : mk(scal<T>::from_double(1.0), scal<T>::zero());
+        cplx<T> wk, wnk;
+        rfft_post(buf[k], buf[nk], tw, wk, wnk);
+        const cplx<df64> a = c_mul(su[k], mk(scal<T>::to_df(wk.re), scal<T>::to_df(wk.im)));
+        acc[k] = c_add(acc[k], mk(df_mul(a.re, sg), df_mul(a.im, sg)));
+        if (n - k != k) {
+          const cplx<df64> b = c_mul(su[n - k], mk(scal<T>::to_df(wnk.re), scal<T>::to_df(wnk.im)));
+          acc[n - k] = c_add(acc[n - k], mk(df_mul(b.re, sg), df_mul(b.im, sg)));
+        }
+      }
+      __syncthreads();
+    }
+    // inverse: acc holds 4 sum sigma U V; irfft_pre doubles it; the inverse FFT scales by n
+    for (int k = threadIdx.x; k <= n / 2; k += BT) {
+      const int nk = (n - k) & (n - 1);
+      const cplx<T> tw = k ? twiddle_M<T>(g.tA, g.tB, g.tws, (int64_t)k << g.twshift)
+                           : mk(scal<T>::from_double(1.0), scal<T>::zero());
+      const cplx<T> pk = mk(scal<T>::from_df(acc[k].re), scal<T>::from_df(acc[k].im));
+      const cplx<T> pnk = mk(scal<T>::from_df(acc[n - k].re), scal<T>::from_df(acc[n - k].im));
+      cplx<T> zk, znk;
+      irfft_pre(pk, pnk, tw, zk, znk);
+      buf[k] = zk;
+      if (k != 0 && nk != k) buf[nk] = znk;
+    }
+    __syncthreads();
+    cta_fft<T, BT, MAXE, true>(buf, g.lg_n, 1, g.tw, g.lg_P);
+    double* o = cx.out + cx.out_off[si] + (int64_t)grp * S.N;
+    const double scale = 1.0 / (8.0 * (double)n);
+    const int64_t mn = S.L < S.K ? S.L : S.K;
+    for (int64_t t = threadIdx.x; t < S.N; t += BT) {
+      const cplx<T> z = buf[t >> 1];
+      const double p = df_to_double(scal<T>::to_df((t & 1) ? z.im : z.re));
+      int64_t c = t + 1;
+      if (S.N - t < c) c = S.N - t;
+      if (mn < c) c = mn;
+      o[t] = p * scale / (double)c;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace ssa
 
 using namespace ssa;
@@ -781,6 +907,8 @@ struct ssa_batch_s {
   double *U = nullptr, *V = nullptr, *sigma = nullptr, *resid = nullptr;
   int64_t totU = 0, totV = 0, totS = 0;
   cudaStream_t stream = nullptr;  // outputs are stream-ordered allocations on this stream
+  int precision = SSA_PREC_F64;
+  int lg_Mmax = 2;
 };
 
 static int bfail(int code, const char* msg) {
@@ -916,6 +1044,7 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
     const double cb = (double)b->ser[c2].N * b->ser[c2].d * b->ser[c2].d;
     return ca > cb;
   });
+  b->lg_Mmax = lgMmax;
   // twiddle tables for the largest transform
   const int64_t Mmax = (int64_t)1 << lgMmax;
   const int lg_P = lgMmax - 1;
@@ -928,6 +1057,7 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
   for (int64_t m = 0; m < nB; ++m) hB[m] = b_tw(m, Mmax);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(o.stream);
   b->stream = s;
+  b->precision = o.precision;
   int dev = 0, sms = 0;
   BCK(cudaGetDevice(&dev));
   BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1065,6 +1195,121 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
   if (worst == SSA_ENUMERIC) host_set_error("non-finite value in a batched series");
   if (worst == SSA_ENOCONV) host_set_error("a batched series did not converge within max_restarts");
   return worst;
+}
+
+namespace ssa {
+const double* batch_device_U(ssa_batch_t b) { return b ? b->U : nullptr; }
+}  // namespace ssa
+
+extern "C" int ssa_batch_reconstruct(ssa_batch_t b, const int32_t* grp_off, const int32_t* grp_idx, int m,
+                                     double* out) {
+  if (!b || !grp_off || !grp_idx || !out || m < 1) return bfail(SSA_EINVAL, "NULL argument or m < 1");
+  std::vector<int32_t> off, idx;
+  int rc = to_host(grp_off, (size_t)m + 1, off);
+  if (rc) return rc;
+  if (off[0] != 0 || off[m] < 0) return bfail(SSA_EINVAL, "bad group offsets");
+  rc = to_host(grp_idx, (size_t)std::max(off[m], 1), idx);
+  if (rc) return rc;
+  int kmin = 1 << 30;
+  for (const BSeries& S : b->ser) kmin = std::min(kmin, S.k);
+  std::vector<char> seen(kmin, 0);
+  for (int gi = 0; gi < m; ++gi) {
+    if (off[gi + 1] < off[gi]) return bfail(SSA_EINVAL, "bad group offsets");
+    for (int a = off[gi]; a < off[gi + 1]; ++a) {
+      if (idx[a] < 0 || idx[a] >= kmin) return bfail(SSA_EINVAL, "group index out of range for some series");
+      if (seen[idx[a]]) return bfail(SSA_EINVAL, "groups overlap");
+      seen[idx[a]] = 1;
+    }
+  }
+  cudaStream_t s = b->stream;
+  const int n = b->nseries;
+  std::vector<int64_t> oo(n);
+  int64_t tot = 0;
+  int nmax = 2;
+  for (int i = 0; i < n; ++i) {
+    oo[i] = tot;
+    tot += (int64_t)m * b->ser[i].N;
+    nmax = std::max(nmax, 1 << b->ser[i].lg_n);
+  }
+  const int lgMmax = b->lg_Mmax;
+  const int64_t Mmax = (int64_t)1 << lgMmax;
+  const int lg_P = lgMmax - 1;
+  const int64_t P = (int64_t)1 << lg_P;
+  const int tws = (lgMmax + 1) / 2;
+  const int64_t nA = Mmax >> tws, nB = (int64_t)1 << tws;
+  std::vector<cplx<df64>> htw(P), hA(nA), hB(nB);
+  for (int64_t q = 0; q < P; ++q) htw[q] = b_tw(q, P);
+  for (int64_t q = 0; q < nA; ++q) hA[q] = b_tw(q << tws, Mmax);
+  for (int64_t q = 0; q < nB; ++q) hB[q] = b_tw(q, Mmax);
+  int dev = 0, sms = 0;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int items = n * m;
+  const int nblk = std::min(sms, items);
+  const int64_t ld_scr = 2 * ((int64_t)nmax + 1);
+  struct Bufs {
+    cudaStream_t s;
+    void* p[8] = {nullptr};
+    ~Bufs() {
+      for (void* q : p)
+        if (q) cudaFreeAsync(q, s);
+    }
+  } bf{s};
+  BCK(cudaMallocAsync(&bf.p[0], P * sizeof(cplx<df64>), s));
+  BCK(cudaMallocAsync(&bf.p[1], nA * sizeof(cplx<df64>), s));
+  BCK(cudaMallocAsync(&bf.p[2], nB * sizeof(cplx<df64>), s));
+  BCK(cudaMallocAsync(&bf.p[3], (size_t)nblk * ld_scr * sizeof(cplx<df64>), s));
+  BCK(cudaMallocAsync(&bf.p[4], (m + 1 + off[m] + 1) * sizeof(int), s));
+  BCK(cudaMallocAsync(&bf.p[5], n * sizeof(int64_t) + n * sizeof(BSeries) + 16, s));
+  BCK(cudaMallocAsync(&bf.p[6], sizeof(int), s));
+  const bool odev = b_on_device(out);
+  if (!odev) BCK(cudaMallocAsync(&bf.p[7], tot * sizeof(double), s));
+  int* dgrp = static_cast<int*>(bf.p[4]);
+  int64_t* doo = static_cast<int64_t*>(bf.p[5]);
+  BSeries* dser = reinterpret_cast<BSeries*>(doo + n);
+  BCK(cudaMemcpyAsync(bf.p[0], htw.data(), P * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(bf.p[1], hA.data(), nA * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(bf.p[2], hB.data(), nB * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(dgrp, off.data(), (m + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(dgrp + m + 1, idx.data(), std::max(off[m], 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(doo, oo.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(dser, b->ser.data(), n * sizeof(BSeries), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemsetAsync(bf.p[6], 0, sizeof(int), s));
+  BHCtx cx{};
+  cx.ser = dser;
+  cx.nseries = n;
+  cx.m = m;
+  cx.U = b->U;
+  cx.V = b->V;
+  cx.sigma = b->sigma;
+  cx.grp_off = dgrp;
+  cx.grp_idx = dgrp + m + 1;
+  cx.out = odev ? out : static_cast<double*>(bf.p[7]);
+  cx.out_off = doo;
+  cx.tw = static_cast<cplx<df64>*>(bf.p[0]);
+  cx.lg_P = lg_P;
+  cx.tA = static_cast<cplx<df64>*>(bf.p[1]);
+  cx.tB = static_cast<cplx<df64>*>(bf.p[2]);
+  cx.tws = tws;
+  cx.lg_Mmax = lgMmax;
+  cx.scratch = static_cast<cplx<df64>*>(bf.p[3]);
+  cx.ld_scr = ld_scr;
+  cx.next = static_cast<int*>(bf.p[6]);
+  prof_begin(s);
+  if (b->precision == SSA_PREC_F32C) {
+    auto kern = k_batch_hankel<float, 16384>;
+    BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
+    kern<<<nblk, BT, B_SMEM, s>>>(cx);
+  } else {
+    auto kern = k_batch_hankel<df64, 8192>;
+    BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
+    kern<<<nblk, BT, B_SMEM, s>>>(cx);
+  }
+  prof_end(s, K_HANKEL_SMALL, 8.0 * (double)(b->totU + b->totV) + 8.0 * (double)tot, 0.0);
+  BCK(cudaGetLastError());
+  if (!odev) BCK(cudaMemcpyAsync(out, bf.p[7], tot * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BCK(cudaStreamSynchronize(s));
+  return SSA_OK;
 }
 
 extern "C" int ssa_batch_info(ssa_batch_t b, int i, int* k, int* converged, int* restarts, int64_t* matvecs) {

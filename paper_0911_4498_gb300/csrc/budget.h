@@ -19,3 +19,11 @@ int64_t batch_path_bytes(const std::vector<BatchItem>& items, int refine);
 bool batch_eligible(int64_t N, int64_t L, int k, int precision);
 
 }  // namespace ssa
+
+// device array of all left vectors of a batch (series after series, each
+// L x k column-major in submission order); valid until ssa_batch_destroy
+typedef struct ssa_batch_s* ssa_batch_t;
+namespace ssa {
+const double* batch_device_U(ssa_batch_t b);
+
+}  // namespace ssa

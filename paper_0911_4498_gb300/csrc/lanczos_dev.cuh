@@ -136,12 +136,24 @@ SSA_D void svd_jacobi_body(const df64* __restrict__ B, int ldb, int r, int c, df
                                                            df64* __restrict__ Qv, double* __restrict__ resid,
                                                            double* __restrict__ sigma_d, int k, double tol_conv,
                                                            int* conv, df64* est, unsigned* status, int max_sweeps,
-                                                           float rot_tol, int warm) {
+                                                           float rot_tol, int warm, df64* stage) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = THREADS / 32;
   __shared__ int rotated;
   __shared__ int sweeps_used;
   __shared__ int ok;
-  // A = B[:r, :c] in column-major, W = I (unless k_svd_precondition left A = B W, W)
+  // With stage (r*c + c*c df64 of shared memory) the sweeps run there: every
+  // rotation reads and writes two columns, and L2 latency would dominate.
+  if (stage) {
+    df64* As = stage;
+    df64* Ws = stage + (int64_t)r * c;
+    if (warm) {
+      for (int e = threadIdx.x; e < r * c; e += THREADS) As[e] = A[e];
+      for (int e = threadIdx.x; e < c * c; e += THREADS) Ws[e] = W[e];
+    }
+    A = As;
+    W = Ws;
+  }
+  // A = B[:r, :c] in column-major, W = I (unless the preconditioner left A = B W, W)
   if (!warm) {
     for (int e = threadIdx.x; e < r * c; e += THREADS) {
       const int i = e % r, j = e / r;

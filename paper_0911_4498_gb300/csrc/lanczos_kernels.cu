@@ -496,9 +496,10 @@ __global__ void __launch_bounds__(SVD_THREADS) k_small_svd(const df64* __restric
                                                            df64* __restrict__ Qv, double* __restrict__ resid,
                                                            double* __restrict__ sigma_d, int k, double tol_conv,
                                                            int* conv, df64* est, unsigned* status, int max_sweeps,
-                                                           float rot_tol, int warm) {
+                                                           float rot_tol, int warm, int staged) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   svd_jacobi_body<SVD_THREADS>(B, ldb, r, c, A, W, cc, sigma, P, Qv, resid, sigma_d, k, tol_conv, conv, est, status,
-                               max_sweeps, rot_tol, warm);
+                               max_sweeps, rot_tol, warm, staged ? reinterpret_cast<df64*>(smem_raw) : nullptr);
 }
 
 __global__ void __launch_bounds__(PRE_THREADS) k_svd_precondition(const df64* __restrict__ B, int ldb, int r, int c,
@@ -786,14 +787,22 @@ void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, 
       attr = true;
     }
     prof_begin(s);
-    k_svd_precondition<<<1, PRE_THREADS, pre_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc, 40, 2e-6f);
+    // FP32 sweeps stop improving near FP32 resolution; the df64 sweeps finish from there
+    k_svd_precondition<<<1, PRE_THREADS, pre_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc, PRE_SWEEPS, 2e-6f);
     prof_end(s, K_SVD_PRE, 0.0, 0.0);
     warm = 1;
   }
+  const size_t st_sm = ((size_t)r * c + (size_t)c * c) * sizeof(df64);
+  const int staged = st_sm <= (size_t)SVD_STAGE_MAX ? 1 : 0;
+  static bool attr2 = false;
+  if (!attr2) {
+    cudaFuncSetAttribute(k_small_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, SVD_STAGE_MAX);
+    attr2 = true;
+  }
   prof_begin(s);
-  k_small_svd<<<1, SVD_THREADS, 0, s>>>(B, ldb, r, c, sw.A, sw.W, cc, sw.sigma, sw.P, sw.Q, sw.resid,
-                                         sw.sigma_d, k, tol_conv, sw.conv, est, status, sw.max_sweeps, sw.rot_tol,
-                                         warm);
+  k_small_svd<<<1, SVD_THREADS, staged ? st_sm : 0, s>>>(B, ldb, r, c, sw.A, sw.W, cc, sw.sigma, sw.P, sw.Q,
+                                                         sw.resid, sw.sigma_d, k, tol_conv, sw.conv, est, status,
+                                                         sw.max_sweeps, sw.rot_tol, warm, staged);
   prof_end(s, K_SMALL_SVD, 0.0, 0.0);
 }
 
