@@ -58,6 +58,10 @@ WORKLOADS = {
     "hmatrix_N4000": dict(kind="hmatrix", N=4000, seed=0),
     # section 6.3: replicas of the rank-5 series + N(0, 5^2), L = N/2, rank-5 reconstruction each
     "bootstrap_N4000_R64": dict(kind="bootstrap", N=4000, R=64),
+    # precision stress: N = 2^22, L = 2^21, k = 100, exact-rank-40 damped cosines + N(0, 1e-6^2);
+    # both precisions, per-sigma errors
+    "damped_N4M_k100": dict(kind="precision", N=1 << 22, L=1 << 21, k=100, gen="damped_sines", seed=3,
+                            golden="tests/golden/sigma_damped_sines_N4194304_L2097152_k100.txt"),
 }
 
 # ncu DRAM traffic of the dominant kernel as a ratio to its algorithmic bytes
@@ -668,6 +672,71 @@ def run_gpu_bootstrap(args, w):
     return 0
 
 
+def run_gpu_precision(args, w):
+    import torch
+    from paper_0911_4498_gb300 import build
+    build.build()
+    import paper_0911_4498_gb300 as ssa
+    N, L, k = w["N"], w["L"], w["k"]
+    f = series(w)
+    fd = torch.from_numpy(f).cuda()
+    stream = torch.cuda.current_stream()
+    signal = 40
+    groups = [list(range(signal)), list(range(signal, k))]   # disjoint: signal, the rest
+    goff, gidx = ssa.groups_csr(groups)
+    res = {}
+    for name, prec in (("f64", ssa.SSA_PREC_F64), ("f32c", ssa.SSA_PREC_F32C)):
+        plan = ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=prec, stream=stream.cuda_stream))
+        sig = torch.empty(k, dtype=torch.float64, device="cuda")
+        rec = torch.empty((2, N), dtype=torch.float64, device="cuda")
+        info = {}
+
+        def step():
+            d, rc = ssa.ssa_decompose(plan, fd, k)
+            try:
+                ssa.ssa_reconstruct(d, goff, gidx, 2, rec)
+                ssa.ssa_decomp_get(d, sig, None, None, None)
+                info.update(ssa.ssa_decomp_info(d))
+                info["rc"] = rc
+            finally:
+                ssa.ssa_decomp_destroy(d)
+
+        ms, clocks = _timed(step, args.steps, args.warmup)
+        res[name] = {"ms": ms, "sigma": sig.cpu().numpy(), "rec": rec.cpu().numpy(), "info": dict(info),
+                     "clocks": clocks}
+        ssa.ssa_plan_destroy(plan)
+    a, b = res["f64"]["sigma"], res["f32c"]["sigma"]
+    gold = read_golden(w.get("golden"))
+
+    def errs(x, ref):
+        return {"rel_sigma_i": [float(v) for v in np.abs(x - ref) / np.abs(ref)],
+                "rel_sigma_1": [float(v) for v in np.abs(x - ref) / abs(ref[0])],
+                "max_rel_signal": float(np.max(np.abs(x[:signal] - ref[:signal]) / ref[:signal])),
+                "max_rel_sigma_1": float(np.max(np.abs(x - ref)) / abs(ref[0]))}
+
+    out = {"f32c_vs_f64": errs(b, a)}
+    if gold is not None:
+        out["f64_vs_oracle"] = errs(a, gold["sigma"][:k])
+        out["f32c_vs_oracle"] = errs(b, gold["sigma"][:k])
+    r64, r32 = res["f64"]["rec"], res["f32c"]["rec"]
+    rec_err = {"signal_group_f32c_vs_f64": float(np.linalg.norm(r32[0] - r64[0]) / np.linalg.norm(r64[0])),
+               "all_k_f32c_vs_f64": float(np.linalg.norm(r32.sum(0) - r64.sum(0)) / np.linalg.norm(r64.sum(0))),
+               "signal_group_f64_vs_series": float(np.linalg.norm(r64[0] - f) / np.linalg.norm(f))}
+    line = {"metric": METRIC, "value": 1000.0 / res["f64"]["ms"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["f64"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "df64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "L": L, "k": k, "signal_rank": signal,
+                       "groups": "first 40 (signal) and the other 60", "l2": "bases ~13 GB, larger than L2"},
+            "modes": {m: {"value": 1000.0 / res[m]["ms"], "ms": res[m]["ms"], "restarts": res[m]["info"]["restarts"],
+                          "matvecs": res[m]["info"]["matvecs"], "converged": res[m]["info"]["rc"] == 0}
+                      for m in res},
+            "sigma_errors": out, "reconstruction_rel_l2": rec_err,
+            "oracle_reference": "present" if gold is not None else "not yet computed",
+            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": res["f64"]["clocks"]}
+    print(json.dumps(line))
+    return 0
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -692,6 +761,8 @@ def run_gpu(args):
         return run_gpu_hmatrix(args, w)
     if w.get("kind") == "bootstrap":
         return run_gpu_bootstrap(args, w)
+    if w.get("kind") == "precision":
+        return run_gpu_precision(args, w)
     N, L, k = w["N"], w["L"], w["k"]
     K = N - L + 1
     prec = ssa.SSA_PREC_F32C if args.precision == "f32c" else ssa.SSA_PREC_F64
