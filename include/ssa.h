@@ -293,6 +293,15 @@ void ssa_serve_destroy(ssa_server_t srv);
 
 /* ---- launch accounting (not part of the paper's method) ---------------- */
 
+/*
+ * Column tiling picked by the four-step autotuner for series of length N in
+ * this precision: columns per CTA of the forward and inverse column passes
+ * (0 when that size has not been planned yet in this process).  Plans with
+ * M/2 above the single-CTA limit time the candidate tilings once per process
+ * at ssa_embed_plan; every tiling gives bitwise the same results.
+ */
+int ssa_fft_tiling(int precision, int64_t N, int* cols_fwd, int* cols_inv);
+
 /* One entry per kernel of the library: launches, summed device time from
    CUDA events recorded around each launch, and the algorithmic bytes and
    flops charged to those launches (what the method must move / compute,

@@ -90,6 +90,7 @@ _SIGS = {
     "ssa_serve_take": (_I, [_VP, _I64, _VP, _VP, _VP, _VP, ctypes.POINTER(ServeInfo)]),
     "ssa_serve_stats": (_I, [_VP, ctypes.POINTER(ServeStats)]),
     "ssa_serve_destroy": (None, [_VP]),
+    "ssa_fft_tiling": (_I, [_I, _I64, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "ssa_stats_enable": (_I, [_I]),
     "ssa_stats_get": (_I, [ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "ssa_kernel_launches": (ctypes.c_uint64, []),
@@ -314,6 +315,13 @@ def ssa_serve_stats(srv) -> dict:
 
 def ssa_serve_destroy(srv):
     lib().ssa_serve_destroy(srv)
+
+
+def ssa_fft_tiling(precision: int, N: int):
+    """(columns per CTA of the forward, inverse four-step column pass); 0 = not tuned yet."""
+    a, b = _I(), _I()
+    _check(lib().ssa_fft_tiling(precision, N, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def ssa_stats_enable(on: bool):

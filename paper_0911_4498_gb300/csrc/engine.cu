@@ -486,7 +486,26 @@ extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_
   g.tw = p->tw;
   g.tA = p->tA;
   g.tB = p->tB;
+  if (!p->small) {  // pick the column tiling of the four-step passes for this n (once per process)
+    const int e = autotune_fourstep(g, o.precision, p->stream);
+    if (e != 0) {
+      set_err("four-step tiling autotune: %s", cudaGetErrorString((cudaError_t)e));
+      return fail(SSA_ECUDA);
+    }
+  }
   *out = p;
+  return SSA_OK;
+}
+
+extern "C" int ssa_fft_tiling(int precision, int64_t N, int* cols_fwd, int* cols_inv) {
+  REQ(cols_fwd != nullptr && cols_inv != nullptr, "NULL argument");
+  REQ(N > 2, "need N > 2");
+  int64_t M = 4;
+  while (M < N) M *= 2;
+  const int lg_n = ilog2(M) - 1;
+  const int a = tuned_tiling(precision, lg_n, 0), b = tuned_tiling(precision, lg_n, 1);
+  *cols_fwd = a >= 0 ? 1 << a : 0;
+  *cols_inv = b >= 0 ? 1 << b : 0;
   return SSA_OK;
 }
 

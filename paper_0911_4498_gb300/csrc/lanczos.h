@@ -8,11 +8,13 @@ constexpr int RT = 256;              // threads per reorthogonalisation block
 constexpr int RP = 4;                // row pairs per thread
 constexpr int SLAB = 2 * RT * RP;    // rows per block
 constexpr int MAXCOL = 512;          // largest basis size (Krylov dimension + 1)
-constexpr int SVD_THREADS = 512;
+constexpr int SVD_THREADS = 1024;
 constexpr int PRE_THREADS = 1024;
 constexpr int PRE_SMEM_MAX = 200 * 1024;  // FP32 preconditioning of the projected SVD when r*c + c*c floats fit
 constexpr int PRE_SWEEPS = 12;          // FP32 preconditioner sweeps at most
 constexpr int SVD_STAGE_MAX = 200 * 1024;  // shared memory for the df64 Jacobi (A and W staged when they fit)
+constexpr int SVD_CL = 8;                  // CTAs of the clustered projected-SVD kernel (portable cluster size)
+constexpr int SVD_CL_THREADS = 512;        // threads per CTA of that kernel
 constexpr int FUSED_MAXCOL = 200;   // largest basis for the fused update+projection pass
 
 struct ReorthWork {

@@ -166,8 +166,12 @@ SSA_D void svd_jacobi_body(const df64* __restrict__ B, int ldb, int r, int c, df
   }
   if (threadIdx.x == 0) sweeps_used = -1;
   __syncthreads();
+  __shared__ float max_ratio;  // largest |gamma| / sqrt(alpha beta) of the sweep
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
+    if (threadIdx.x == 0) {
+      rotated = 0;
+      max_ratio = 0.f;
+    }
     __syncthreads();
     for (int rnd = 0; rnd < cc - 1; ++rnd) {
       for (int pr = warp; pr < cc / 2; pr += nw) {
@@ -189,8 +193,13 @@ SSA_D void svd_jacobi_body(const df64* __restrict__ B, int ldb, int r, int c, df
         if (!(al.hi > 0.f) || !(be.hi > 0.f)) continue;
         // rotate when |gamma| > tol sqrt(alpha) sqrt(beta) (square roots keep
         // the test inside the float exponent range)
-        const df64 thr = df_mul_f(df_mul(df_sqrt(al), df_sqrt(be)), rot_tol);
+        const df64 nab = df_mul(df_sqrt(al), df_sqrt(be));
+        const df64 thr = df_mul_f(nab, rot_tol);
         if (!df_gt(df_abs(ga), thr)) continue;
+        if (lane == 0) {  // non-negative floats order like their bit patterns
+          const float ratio = fabsf(ga.hi) / nab.hi;
+          atomicMax(reinterpret_cast<int*>(&max_ratio), __float_as_int(ratio));
+        }
         const df64 zeta = df_div(df_sub(be, al), df_scale(ga, 2.f));
         const df64 az = df_abs(zeta);
         df64 t;
@@ -219,8 +228,12 @@ SSA_D void svd_jacobi_body(const df64* __restrict__ B, int ldb, int r, int c, df
       __syncthreads();
     }
     const int any = rotated;
+    const float mr = max_ratio;
     __syncthreads();
-    if (!any) {
+    // no rotation, or every rotation of this sweep below 1e-10: with the
+    // quadratic convergence of cyclic Jacobi the next sweep's rotations would
+    // be far below rot_tol, so that sweep is skipped
+    if (!any || mr < 1e-10f) {
       if (threadIdx.x == 0) sweeps_used = sweep + 1;
       break;
     }

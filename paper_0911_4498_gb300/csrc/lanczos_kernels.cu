@@ -502,6 +502,165 @@ __global__ void __launch_bounds__(SVD_THREADS) k_small_svd(const df64* __restric
                                max_sweeps, rot_tol, warm, staged ? reinterpret_cast<df64*>(smem_raw) : nullptr);
 }
 
+// One-sided Jacobi of the projected matrix on a cluster of SVD_CL CTAs: the
+// columns of A (r each) and W (c each) live in the CTAs' shared memory,
+// column j in CTA j % SVD_CL (distributed shared memory); each rotation pair
+// of a round is one warp anywhere in the cluster, and the hardware cluster
+// barrier separates the rounds.  The arithmetic of every pair is that of
+// svd_jacobi_body (same order, same reductions), so the results are the
+// same bit for bit; the work of a round is spread over SVD_CL SMs instead of
+// one.
+__global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
+    k_small_svd_cluster(const df64* __restrict__ B, int ldb, int r, int c, const df64* __restrict__ Ain,
+                        const df64* __restrict__ Win, int cc, df64* __restrict__ sigma, df64* __restrict__ P,
+                        df64* __restrict__ Qv, double* __restrict__ resid, double* __restrict__ sigma_d, int k,
+                        double tol_conv, int* conv, df64* est, unsigned* status, int max_sweeps, float rot_tol,
+                        int warm) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nloc = (c + SVD_CL - 1) / SVD_CL;
+  df64* Aloc = reinterpret_cast<df64*>(smem_raw);
+  df64* Wloc = Aloc + (size_t)nloc * r;
+  df64* nrm_loc = Wloc + (size_t)nloc * c;
+  __shared__ int rotated_s;
+  __shared__ float maxr_s;
+  __shared__ int ok_s;
+  const int lane = threadIdx.x & 31, nwl = SVD_CL_THREADS / 32;
+  const int gwarp = rank * nwl + (threadIdx.x >> 5), nwarps = SVD_CL * nwl;
+  auto colA = [&](int j) { return cl.map_shared_rank(Aloc + (size_t)(j / SVD_CL) * r, j % SVD_CL); };
+  auto colW = [&](int j) { return cl.map_shared_rank(Wloc + (size_t)(j / SVD_CL) * c, j % SVD_CL); };
+  for (int jl = 0; jl < nloc; ++jl) {
+    const int j = jl * SVD_CL + rank;
+    if (j >= c) break;
+    for (int i = threadIdx.x; i < r; i += SVD_CL_THREADS)
+      Aloc[(size_t)jl * r + i] = warm ? Ain[(size_t)j * r + i] : B[(size_t)i * ldb + j];
+    for (int i = threadIdx.x; i < c; i += SVD_CL_THREADS)
+      Wloc[(size_t)jl * c + i] = warm ? Win[(size_t)j * c + i] : make_df(i == j ? 1.f : 0.f, 0.f);
+  }
+  cl.sync();
+  int sweeps_used = -1;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) {
+      rotated_s = 0;
+      maxr_s = 0.f;
+    }
+    __syncthreads();
+    for (int rnd = 0; rnd < cc - 1; ++rnd) {
+      for (int pr = gwarp; pr < cc / 2; pr += nwarps) {
+        const int2 pq = rr_pair(rnd, pr, cc);
+        const int p = pq.x, q = pq.y;
+        if (p >= c || q >= c) continue;
+        df64* ap = colA(p);
+        df64* aq = colA(q);
+        df64 al = df_zero(), be = df_zero(), ga = df_zero();
+        for (int i = lane; i < r; i += 32) {
+          const df64 x = ap[i], y = aq[i];
+          al = df_fma(x, x, al);
+          be = df_fma(y, y, be);
+          ga = df_fma(x, y, ga);
+        }
+        al = warp_sum_df(al);
+        be = warp_sum_df(be);
+        ga = warp_sum_df(ga);
+        if (!(al.hi > 0.f) || !(be.hi > 0.f)) continue;
+        const df64 nab = df_mul(df_sqrt(al), df_sqrt(be));
+        const df64 thr = df_mul_f(nab, rot_tol);
+        if (!df_gt(df_abs(ga), thr)) continue;
+        if (lane == 0) {
+          const float ratio = fabsf(ga.hi) / nab.hi;
+          atomicMax(reinterpret_cast<int*>(&maxr_s), __float_as_int(ratio));
+        }
+        const df64 zeta = df_div(df_sub(be, al), df_scale(ga, 2.f));
+        const df64 az = df_abs(zeta);
+        df64 t;
+        if (az.hi > 1e15f) {
+          t = df_div(make_df(1.f, 0.f), df_scale(zeta, 2.f));
+        } else {
+          t = df_div(make_df(zeta.hi >= 0.f ? 1.f : -1.f, 0.f),
+                     df_add(az, df_sqrt(df_add(make_df(1.f, 0.f), df_mul(zeta, zeta)))));
+        }
+        const df64 cs = df_div(make_df(1.f, 0.f), df_sqrt(df_add(make_df(1.f, 0.f), df_mul(t, t))));
+        const df64 sn = df_mul(cs, t);
+        for (int i = lane; i < r; i += 32) {
+          const df64 x = ap[i], y = aq[i];
+          ap[i] = df_sub(df_mul(cs, x), df_mul(sn, y));
+          aq[i] = df_add(df_mul(sn, x), df_mul(cs, y));
+        }
+        df64* wp = colW(p);
+        df64* wq = colW(q);
+        for (int i = lane; i < c; i += 32) {
+          const df64 x = wp[i], y = wq[i];
+          wp[i] = df_sub(df_mul(cs, x), df_mul(sn, y));
+          wq[i] = df_add(df_mul(sn, x), df_mul(cs, y));
+        }
+        if (lane == 0) rotated_s = 1;
+      }
+      cl.sync();
+    }
+    int any = 0;
+    float mr = 0.f;
+    for (int qr = 0; qr < SVD_CL; ++qr) {
+      any |= *cl.map_shared_rank(&rotated_s, qr);
+      mr = fmaxf(mr, *cl.map_shared_rank(&maxr_s, qr));
+    }
+    cl.sync();  // every CTA has read the flags before they are reset
+    if (!any || mr < 1e-10f) {
+      sweeps_used = sweep + 1;
+      break;
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0 && sweeps_used < 0) atomicOr(status, SSA_DEV_JACOBI_NOCONV);
+  // column norms of the local columns
+  for (int jl = threadIdx.x >> 5; jl < nloc; jl += nwl) {
+    const int j = jl * SVD_CL + rank;
+    if (j >= c) break;
+    df64 sq = df_zero();
+    for (int i = lane; i < r; i += 32) sq = df_fma(Aloc[(size_t)jl * r + i], Aloc[(size_t)jl * r + i], sq);
+    sq = warp_sum_df(sq);
+    if (lane == 0) nrm_loc[jl] = df_sqrt(sq);
+  }
+  cl.sync();
+  // rank by descending sigma (ties: lower index first); the owner scatters its columns
+  for (int jl = threadIdx.x >> 5; jl < nloc; jl += nwl) {
+    const int j = jl * SVD_CL + rank;
+    if (j >= c) break;
+    const df64 sj = nrm_loc[jl];
+    int rk = 0;
+    for (int i = lane; i < c; i += 32) {
+      const df64 si = *cl.map_shared_rank(nrm_loc + i / SVD_CL, i % SVD_CL);
+      if (df_gt(si, sj) || (si.hi == sj.hi && si.lo == sj.lo && i < j)) ++rk;
+    }
+    for (int m = 16; m; m >>= 1) rk += __shfl_xor_sync(0xffffffffu, rk, m);
+    const df64 inv = sj.hi > 0.f ? df_div(make_df(1.f, 0.f), sj) : df_zero();
+    for (int i = lane; i < r; i += 32) P[(size_t)rk * r + i] = df_mul(Aloc[(size_t)jl * r + i], inv);
+    for (int i = lane; i < c; i += 32) Qv[(size_t)rk * c + i] = Wloc[(size_t)jl * c + i];
+    if (lane == 0) {
+      sigma[rk] = sj;
+      sigma_d[rk] = df_to_double(sj);
+    }
+  }
+  cl.sync();
+  if (rank != 0) return;
+  // residuals from relation (2) and the convergence test
+  const df64 alpha_res = B[(int64_t)(r - 1) * ldb + c];
+  if (threadIdx.x == 0) ok_s = 1;
+  __syncthreads();
+  const double s1 = sigma_d[0];
+  for (int m = threadIdx.x; m < c; m += SVD_CL_THREADS) {
+    const double rm = fabs(df_to_double(df_mul(alpha_res, P[(int64_t)m * r + (r - 1)])));
+    resid[m] = rm;
+    if (m < k && !(rm <= tol_conv * s1)) ok_s = 0;
+    if (!isfinite(rm)) atomicOr(status, SSA_DEV_NONFINITE);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *conv = ok_s;
+    if (df_gt(sigma[0], *est)) *est = sigma[0];
+  }
+}
+
 __global__ void __launch_bounds__(PRE_THREADS) k_svd_precondition(const df64* __restrict__ B, int ldb, int r, int c,
                                                                   df64* __restrict__ A, df64* __restrict__ W,
                                                                   df64* __restrict__ T1, int cc, int max_sweeps,
@@ -791,6 +950,22 @@ void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, 
     k_svd_precondition<<<1, PRE_THREADS, pre_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc, PRE_SWEEPS, 2e-6f);
     prof_end(s, K_SVD_PRE, 0.0, 0.0);
     warm = 1;
+  }
+  // the cluster version when its share of the columns fits in each CTA
+  const int nloc = (c + SVD_CL - 1) / SVD_CL;
+  const size_t cl_sm = ((size_t)nloc * (r + c) + nloc) * sizeof(df64);
+  if (cl_sm <= (size_t)SVD_STAGE_MAX) {
+    static bool attr3 = false;
+    if (!attr3) {
+      cudaFuncSetAttribute(k_small_svd_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, SVD_STAGE_MAX);
+      attr3 = true;
+    }
+    prof_begin(s);
+    k_small_svd_cluster<<<SVD_CL, SVD_CL_THREADS, cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, cc, sw.sigma, sw.P, sw.Q,
+                                                               sw.resid, sw.sigma_d, k, tol_conv, sw.conv, est,
+                                                               status, sw.max_sweeps, sw.rot_tol, warm);
+    prof_end(s, K_SMALL_SVD, 0.0, 0.0);
+    return;
   }
   const size_t st_sm = ((size_t)r * c + (size_t)c * c) * sizeof(df64);
   const int staged = st_sm <= (size_t)SVD_STAGE_MAX ? 1 : 0;

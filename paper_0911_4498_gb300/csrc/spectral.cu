@@ -17,6 +17,7 @@
 //   min(t+1, L, K, N-t) (Algorithm 4 prints a product with the counts; the
 //   convolution identity of section 5 requires the quotient).
 #include <cstdio>
+#include <atomic>
 #include <mutex>
 #include "spectral.h"
 #include "fft.cuh"
@@ -387,8 +388,8 @@ static int lg2(int64_t x) {
 // COLE: elements per CTA of the four-step column kernels (32 KB, 256 threads),
 // small enough for several CTAs per SM and no register spills.
 template <class T> struct Lim;
-template <> struct Lim<float> { static constexpr int MAXE = 16384; static constexpr int COLE = 4096; };
-template <> struct Lim<df64> { static constexpr int MAXE = 8192; static constexpr int COLE = 2048; };
+template <> struct Lim<float> { static constexpr int MAXE = 16384; static constexpr int COLE = 8192; };
+template <> struct Lim<df64> { static constexpr int MAXE = 8192; static constexpr int COLE = 4096; };
 template <> struct Lim<double> { static constexpr int MAXE = 8192; static constexpr int COLE = 2048; };
 constexpr int TH = 512;
 constexpr int TH_COL = 256;
@@ -434,11 +435,35 @@ int col_lg_cb(const Geom& g, int maxe) {
   return lg;
 }
 
+// Columns per CTA (2^lg_cb) of the four-step column passes.  Every choice
+// gives bitwise the same result (each column's FFT runs the same stages);
+// autotune_fourstep() times the candidates once per (arithmetic type, pass,
+// n) and the launches below use the fastest, else the largest tile.
+template <class T> constexpr int type_slot() { return std::is_same<T, float>::value ? 0 : 1; }
+static std::atomic<int> g_tuned_cb[2][2][32];
+static std::atomic<bool> g_tune_init{false};
+static std::mutex g_tune_mu;
+static void tune_table_init() {
+  if (g_tune_init.load()) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune_init.load()) return;
+  for (auto& a : g_tuned_cb)
+    for (auto& b : a)
+      for (auto& c : b) c.store(-1);
+  g_tune_init.store(true);
+}
+template <class T> static int tuned_lg_cb(const Geom& g, int pass) {
+  const int dflt = col_lg_cb(g, Lim<T>::COLE);
+  if (std::is_same<T, double>::value || !g_tune_init.load()) return dflt;
+  const int v = g_tuned_cb[type_slot<T>()][pass][g.lg_n].load();
+  return v >= 0 && v <= dflt ? v : dflt;
+}
+
 template <class T, int G, class In>
 static void fs_forward(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s,
-                       int cls, double bytes) {
+                       int cls, double bytes, int lg_cb_force = -1) {
   constexpr int MAXE = Lim<T>::COLE;
-  const int lg_cb = col_lg_cb(g, MAXE);
+  const int lg_cb = lg_cb_force >= 0 ? lg_cb_force : tuned_lg_cb<T>(g, 0);
   const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
   auto kern = k_fs_col_fwd<T, TH_COL, MAXE, G, In>;
   set_smem(kern, sm);
@@ -461,9 +486,9 @@ static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cuda
 
 template <class T, int OUTM, class Out>
 static void fs_inverse(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int64_t off, int64_t cnt, float scale,
-                       int batch, cudaStream_t s, int cls, double bytes) {
+                       int batch, cudaStream_t s, int cls, double bytes, int lg_cb_force = -1) {
   constexpr int MAXE = Lim<T>::COLE;
-  const int lg_cb = col_lg_cb(g, MAXE);
+  const int lg_cb = lg_cb_force >= 0 ? lg_cb_force : tuned_lg_cb<T>(g, 1);
   const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
   auto kern = k_fs_col_inv<T, TH_COL, MAXE, OUTM, Out>;
   set_smem(kern, sm);
@@ -639,6 +664,77 @@ void launch_hankel(const Geom& g, int prec, const df64* U, int64_t ldu, const df
     hankel_impl<df64, double>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, grp_off_host, grp_idx_host, m, out,
                               ldo, scratch, sm, s);
   }
+}
+
+// ---- autotuner of the column tiling
+template <class T>
+static int tune_one(const Geom& g, int pass, const df64* x, df64* y, cplx<T>* Y, cudaStream_t s) {
+  const int maxcb = col_lg_cb(g, Lim<T>::COLE);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = maxcb;
+  float best_ms = 1e30f;
+  for (int cb = 0; cb <= maxcb; ++cb) {
+    auto run = [&]() {
+      if (pass == 0) fs_forward<T, GATHER_X, df64>(g, x, 0, 0, Y, 1, s, K_MISC, 0.0, cb);
+      else fs_inverse<T, OUT_SLICE, df64>(g, Y, y, 0, 0, g.L, 1.0f, 1, s, K_MISC, 0.0, cb);
+    };
+    run();  // warm-up (and the shared-memory opt-in)
+    float ms = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, s);
+      for (int i = 0; i < 4; ++i) run();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms = std::min(ms, t);
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+int autotune_fourstep(const Geom& g, int prec, cudaStream_t s) {
+  tune_table_init();
+  if (small_path(g, prec)) return 0;
+  const int slot = prec == PREC_F32C ? 0 : 1;
+  if (g_tuned_cb[slot][0][g.lg_n].load() >= 0 && g_tuned_cb[slot][1][g.lg_n].load() >= 0) return 0;
+  const int64_t n = (int64_t)1 << g.lg_n;
+  void* buf = nullptr;
+  const size_t xb = (size_t)(g.K + g.L + 8) * sizeof(df64);
+  cudaError_t e = cudaMallocAsync(&buf, xb + (size_t)n * sizeof(cplx<df64>), s);
+  if (e != cudaSuccess) return (int)e;
+  cudaMemsetAsync(buf, 0, xb + (size_t)n * sizeof(cplx<df64>), s);
+  df64* x = static_cast<df64*>(buf);
+  df64* y = x + g.K + 4;
+  void* Yv = static_cast<char*>(buf) + xb;
+  prof_suppress(true);
+  int f, i;
+  if (slot == 0) {
+    f = tune_one<float>(g, 0, x, y, static_cast<cplx<float>*>(Yv), s);
+    i = tune_one<float>(g, 1, x, y, static_cast<cplx<float>*>(Yv), s);
+  } else {
+    f = tune_one<df64>(g, 0, x, y, static_cast<cplx<df64>*>(Yv), s);
+    i = tune_one<df64>(g, 1, x, y, static_cast<cplx<df64>*>(Yv), s);
+  }
+  prof_suppress(false);
+  g_tuned_cb[slot][0][g.lg_n].store(f);
+  g_tuned_cb[slot][1][g.lg_n].store(i);
+  cudaFreeAsync(buf, s);
+  return (int)cudaGetLastError();
+}
+
+int tuned_tiling(int prec, int lg_n, int pass) {
+  tune_table_init();
+  if (lg_n < 0 || lg_n >= 32 || pass < 0 || pass > 1) return -1;
+  return g_tuned_cb[prec == PREC_F32C ? 0 : 1][pass][lg_n].load();
 }
 
 size_t spectral_scratch_bytes(const Geom& g) {

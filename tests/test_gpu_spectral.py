@@ -136,3 +136,19 @@ def test_invalid_arguments_are_rejected():
             ssa.ssa_hankelize(plan, np.ones(2), np.ones(80), 40, np.ones(122), 61, 2, off, idx, 2, np.zeros(200))
     finally:
         ssa.ssa_plan_destroy(plan)
+
+
+def test_fourstep_autotuner_picks_a_tiling_and_results_match():
+    """A plan with the four-step path tunes the column tiling once; products
+    with the tuned tiling match the oracle like any other."""
+    ssa_mod = ssa
+    N, L = 300001, 100000
+    for prec, tol in ((ssa_mod.SSA_PREC_F64, 1e-12), (ssa_mod.SSA_PREC_F32C, 1e-5)):
+        f = synth.three_sines(N, seed=11)
+        x = np.random.default_rng(1).standard_normal(N - L + 1)
+        y = gpu_matvec(f, L, x, transpose=False, precision=prec)
+        fw, inv = ssa_mod.ssa_fft_tiling(prec, N)
+        assert fw >= 1 and inv >= 1 and (fw & (fw - 1)) == 0 and (inv & (inv - 1)) == 0
+        M = fast_hankel.fft_length(N)
+        ref = fast_hankel.hankel_matvec(fast_hankel.spectrum(f, L, M), N, L, x)
+        assert np.max(np.abs(y - ref)) <= tol * np.max(np.abs(ref))
