@@ -661,6 +661,133 @@ __global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
   }
 }
 
+// The FP32 preconditioner of the projected SVD on an 8-CTA cluster: FP32
+// one-sided Jacobi with the columns of A32 and W32 spread over the CTAs'
+// shared memory (as k_small_svd_cluster), then the two Newton-Schulz steps
+// and A = B W with their entries split over the cluster's threads.  Same
+// arithmetic per entry as svd_precondition_body.
+__global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
+    k_svd_precondition_cluster(const df64* __restrict__ B, int ldb, int r, int c, df64* __restrict__ A,
+                               df64* __restrict__ W, df64* __restrict__ T1, int cc, int max_sweeps, float tol32) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nloc = (c + SVD_CL - 1) / SVD_CL;
+  float* A32 = reinterpret_cast<float*>(smem_raw);
+  float* W32 = A32 + (size_t)nloc * r;
+  __shared__ int rotated_s;
+  const int lane = threadIdx.x & 31, nwl = SVD_CL_THREADS / 32;
+  const int gwarp = rank * nwl + (threadIdx.x >> 5), nwarps = SVD_CL * nwl;
+  const int gtid = rank * SVD_CL_THREADS + threadIdx.x, gthreads = SVD_CL * SVD_CL_THREADS;
+  auto colA = [&](int j) { return cl.map_shared_rank(A32 + (size_t)(j / SVD_CL) * r, j % SVD_CL); };
+  auto colW = [&](int j) { return cl.map_shared_rank(W32 + (size_t)(j / SVD_CL) * c, j % SVD_CL); };
+  for (int jl = 0; jl < nloc; ++jl) {
+    const int j = jl * SVD_CL + rank;
+    if (j >= c) break;
+    for (int i = threadIdx.x; i < r; i += SVD_CL_THREADS) {
+      const df64 b = B[(int64_t)i * ldb + j];
+      A32[(size_t)jl * r + i] = b.hi + b.lo;
+    }
+    for (int i = threadIdx.x; i < c; i += SVD_CL_THREADS) W32[(size_t)jl * c + i] = i == j ? 1.f : 0.f;
+  }
+  cl.sync();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated_s = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < cc - 1; ++rnd) {
+      for (int pr = gwarp; pr < cc / 2; pr += nwarps) {
+        const int2 pq = rr_pair(rnd, pr, cc);
+        const int p = pq.x, q = pq.y;
+        if (p >= c || q >= c) continue;
+        float* ap = colA(p);
+        float* aq = colA(q);
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int i = lane; i < r; i += 32) {
+          const float x = ap[i], y = aq[i];
+          al = fmaf(x, x, al);
+          be = fmaf(y, y, be);
+          ga = fmaf(x, y, ga);
+        }
+#pragma unroll
+        for (int m = 16; m; m >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, m);
+          be += __shfl_xor_sync(0xffffffffu, be, m);
+          ga += __shfl_xor_sync(0xffffffffu, ga, m);
+        }
+        if (!(al > 0.f) || !(be > 0.f)) continue;
+        if (!(fabsf(ga) > tol32 * sqrtf(al) * sqrtf(be))) continue;
+        const float zeta = (be - al) / (2.f * ga);
+        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float cs = 1.f / sqrtf(1.f + t * t);
+        const float sn = cs * t;
+        for (int i = lane; i < r; i += 32) {
+          const float x = ap[i], y = aq[i];
+          ap[i] = cs * x - sn * y;
+          aq[i] = sn * x + cs * y;
+        }
+        float* wp = colW(p);
+        float* wq = colW(q);
+        for (int i = lane; i < c; i += 32) {
+          const float x = wp[i], y = wq[i];
+          wp[i] = cs * x - sn * y;
+          wq[i] = sn * x + cs * y;
+        }
+        if (lane == 0) rotated_s = 1;
+      }
+      cl.sync();
+    }
+    int any = 0;
+    for (int qr = 0; qr < SVD_CL; ++qr) any |= *cl.map_shared_rank(&rotated_s, qr);
+    cl.sync();
+    if (!any) break;
+  }
+  // Newton-Schulz 1: T1 = W32^T W32 (exact float products, df64 sums); W = W32 (1.5 I - 0.5 T1)
+  for (int e = gtid; e < c * c; e += gthreads) {
+    const int i = e % c, j = e / c;
+    const float* wi = colW(i);
+    const float* wj = colW(j);
+    df64 a = df_zero();
+    for (int q = 0; q < c; ++q) a = df_add(a, two_prod(wi[q], wj[q]));
+    T1[(int64_t)j * c + i] = a;
+  }
+  cl.sync();
+  for (int e = gtid; e < c * c; e += gthreads) {
+    const int row = e % c, j = e / c;
+    df64 a = df_zero();
+    for (int i = 0; i < c; ++i) a = df_fma(make_df(colW(i)[row], 0.f), T1[(int64_t)j * c + i], a);
+    const df64 wkj = make_df(colW(j)[row], 0.f);
+    W[(int64_t)j * c + row] = df_sub(df_mul_f(wkj, 1.5f), df_scale(a, 0.5f));
+  }
+  cl.sync();
+  // Newton-Schulz 2 in df64: T1 = W^T W; A (scratch) = W (1.5 I - 0.5 T1); W = A
+  for (int e = gtid; e < c * c; e += gthreads) {
+    const int i = e % c, j = e / c;
+    const df64* wi = W + (int64_t)i * c;
+    const df64* wj = W + (int64_t)j * c;
+    df64 a = df_zero();
+    for (int q = 0; q < c; ++q) a = df_fma(wi[q], wj[q], a);
+    T1[(int64_t)j * c + i] = a;
+  }
+  cl.sync();
+  for (int e = gtid; e < c * c; e += gthreads) {
+    const int row = e % c, j = e / c;
+    df64 a = df_zero();
+    for (int i = 0; i < c; ++i) a = df_fma(W[(int64_t)i * c + row], T1[(int64_t)j * c + i], a);
+    A[(int64_t)j * c + row] = df_sub(df_mul_f(W[(int64_t)j * c + row], 1.5f), df_scale(a, 0.5f));
+  }
+  cl.sync();
+  for (int e = gtid; e < c * c; e += gthreads) W[e] = A[e];
+  cl.sync();
+  // A = B[:r, :c] W
+  for (int e = gtid; e < r * c; e += gthreads) {
+    const int i = e % r, j = e / r;
+    df64 a = df_zero();
+    for (int q = 0; q < c; ++q) a = df_fma(B[(int64_t)i * ldb + q], W[(int64_t)j * c + q], a);
+    A[(int64_t)j * r + i] = a;
+  }
+}
+
 __global__ void __launch_bounds__(PRE_THREADS) k_svd_precondition(const df64* __restrict__ B, int ldb, int r, int c,
                                                                   df64* __restrict__ A, df64* __restrict__ W,
                                                                   df64* __restrict__ T1, int cc, int max_sweeps,
@@ -939,7 +1066,20 @@ void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, 
   const int cc = c + (c & 1);
   const size_t pre_sm = ((size_t)r * c + (size_t)c * c) * sizeof(float);
   int warm = 0;
-  if (c >= 16 && pre_sm <= (size_t)PRE_SMEM_MAX) {
+  const int nloc_p = (c + SVD_CL - 1) / SVD_CL;
+  const size_t pre_cl_sm = (size_t)nloc_p * (r + c) * sizeof(float);
+  if (c >= 16 && pre_cl_sm <= (size_t)PRE_SMEM_MAX) {
+    static bool attr_c = false;
+    if (!attr_c) {
+      cudaFuncSetAttribute(k_svd_precondition_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, PRE_SMEM_MAX);
+      attr_c = true;
+    }
+    prof_begin(s);
+    k_svd_precondition_cluster<<<SVD_CL, SVD_CL_THREADS, pre_cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc,
+                                                                         PRE_SWEEPS, 2e-6f);
+    prof_end(s, K_SVD_PRE, 0.0, 0.0);
+    warm = 1;
+  } else if (c >= 16 && pre_sm <= (size_t)PRE_SMEM_MAX) {
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_svd_precondition, cudaFuncAttributeMaxDynamicSharedMemorySize, PRE_SMEM_MAX);
