@@ -388,8 +388,8 @@ static int lg2(int64_t x) {
 // COLE: elements per CTA of the four-step column kernels (32 KB, 256 threads),
 // small enough for several CTAs per SM and no register spills.
 template <class T> struct Lim;
-template <> struct Lim<float> { static constexpr int MAXE = 16384; static constexpr int COLE = 8192; };
-template <> struct Lim<df64> { static constexpr int MAXE = 8192; static constexpr int COLE = 4096; };
+template <> struct Lim<float> { static constexpr int MAXE = 16384; static constexpr int COLE = 4096; };
+template <> struct Lim<df64> { static constexpr int MAXE = 8192; static constexpr int COLE = 2048; };
 template <> struct Lim<double> { static constexpr int MAXE = 8192; static constexpr int COLE = 2048; };
 constexpr int TH = 512;
 constexpr int TH_COL = 256;
@@ -476,7 +476,10 @@ static void fs_forward(const Geom& g, const In* x, int64_t ldx, int64_t glen, cp
 template <class T, int MODE>
 static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cudaStream_t s, int cls, double bytes) {
   const size_t sm = (size_t)(2 << g.lg_n2) * sizeof(cplx<T>);
-  auto kern = k_fs_row<T, TH_ROW, MAXE_ROW, MODE>;
+  // the register arrays of the in-place FFT are sized by the bound: use the
+  // smaller instantiation for rows of up to 1024 points
+  auto kern = (2 << g.lg_n2) <= MAXE_ROW / 2 ? k_fs_row<T, TH_ROW, MAXE_ROW / 2, MODE>
+                                             : k_fs_row<T, TH_ROW, MAXE_ROW, MODE>;
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n1) / 2, batch);
   prof_begin(s);
