@@ -69,8 +69,8 @@ WORKLOADS = {
 # size), keyed by the kernel class; valid only while the kernel source is
 # unchanged (sha256 of its file), else the line reports traffic null.
 NCU_TRAFFIC = {
-    "cgs_update_proj": {"ratio": 0.984, "file": "paper_0911_4498_gb300/csrc/lanczos_kernels.cu",
-                        "sha256": "f4186452a50c174bb97f52d4b328f8e024e41f994a5a228ecc3e3af8d29fd97a",
+    "cgs_update_proj": {"ratio": 0.983, "file": "paper_0911_4498_gb300/csrc/cgs.cu",
+                        "sha256": "fe61a56080808ed7077b10c5fcfbfa7bcb62d5af5ec496da6d171195b5d47d79",
                         "profile": "profiles/cgs_tiles_many_sines_N1M_dram.md"},
 }
 
@@ -349,21 +349,33 @@ def run_gpu_batch(args, w):
         return rc, infos
 
     rc, infos = step(f_dev, off_d, L_d, k_d, collect=True)
+    # the timed runs: one batch plan, its run captured once in a CUDA graph and replayed
+    side = torch.cuda.Stream()
+    plan = ssa.ssa_batch_plan(off, Ls, ks32, ssa.make_opts(precision=prec, stream=side.cuda_stream))
+    torch.cuda.synchronize()
+    ssa.ssa_batch_run(plan, f_dev)
+    ssa.ssa_batch_wait(plan)
+    graph = torch.cuda.CUDAGraph()
+    l0 = ssa.ssa_kernel_launches()
+    with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
+        ssa.ssa_batch_run(plan, f_dev)
+    kernels_per_run = ssa.ssa_kernel_launches() - l0
     for _ in range(max(0, args.warmup - 1)):
-        step(f_dev, off_d, L_d, k_d)
+        graph.replay()
     torch.cuda.synchronize()
     sampler = ClockSampler(0)
     sampler.start()
-    launches0 = ssa.ssa_kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step(f_dev, off_d, L_d, k_d)
+        graph.replay()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     clocks = sampler.stop()
-    launches = ssa.ssa_kernel_launches() - launches0
+    assert ssa.ssa_batch_wait(plan) in (ssa.SSA_OK, ssa.SSA_ENOCONV)
+    ssa.ssa_batch_destroy(plan)
+    launches = kernels_per_run * args.steps
     value = n / (ms / 1000.0)
     # end to end with host arrays: H2D of all series inside the call, D2H of every sigma
     f_pin = torch.from_numpy(f_host).pin_memory()
@@ -419,6 +431,7 @@ def run_gpu_batch(args, w):
             "vs_baseline": None, "dtype": "f32+df64" if prec == ssa.SSA_PREC_F32C else "df64", "data": "synthetic",
             "config": {"workload": args.workload, "series": n, "N": "U{500..20000}", "L": "round(N/3) | N//2",
                        "k": "U{4..32}", "total_samples": int(Ns.sum()), "precision": args.precision_batch,
+                       "launch": "ssa_batch_run captured once in a CUDA graph, replayed per step",
                        "l2": "inputs 0.33 GB, larger than L2; no flush"},
             "sigma_rel_err_max_sample": max(errs), "converged": all(i["converged"] for i in infos),
             "matvecs_mean": float(np.mean([i["matvecs"] for i in infos])), "roofline": roof, "cpu_baseline": cpu,
@@ -439,7 +452,8 @@ def run_gpu_serving(args, w):
         arr = synth.serving_arrivals(w["rate"], args.window, seed=w["seed"] + i)
         return [(t, N, L, k, synth.three_sines(N, seed=sd)) for (t, N, L, k, sd) in arr]
 
-    srv = ssa.ssa_serve_create(ssa.make_serve_opts(precision=prec))
+    srv = ssa.ssa_serve_create(ssa.make_serve_opts(precision=prec, workers=args.serve_workers,
+                                                   batch_workers=args.serve_batch_workers))
     sampler = None
     lat, done_n, t_total, nreq, batched = [], 0, 0.0, 0, 0
     launches0 = None
@@ -493,7 +507,8 @@ def run_gpu_serving(args, w):
             "data": "synthetic",
             "config": {"workload": args.workload, "arrival_rate": w["rate"], "window_s": args.window,
                        "N": "log-uniform [1e3, 1e6]", "L": "N//2", "k": "U{2..64}", "mem_budget_GiB": 40,
-                       "precision": args.precision_batch, "outputs": "sigma and residuals"},
+                       "precision": args.precision_batch, "outputs": "sigma and residuals",
+                       "workers": args.serve_workers, "batch_workers": args.serve_batch_workers},
             "requests": nreq, "batched_requests": batched,
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "offered_rps": w["rate"], "sequential_f64": {"value": seq_rate, "requests": len(seq)},
@@ -939,6 +954,8 @@ def main():
                     help="precision of the batch and serving workloads")
     ap.add_argument("--window", type=float, default=0.25, help="serving: arrival window per step (s)")
     ap.add_argument("--seq-sample", type=int, default=40, help="serving: requests timed sequentially in FP64")
+    ap.add_argument("--serve-workers", type=int, default=16, help="serving: single-series workers (streams)")
+    ap.add_argument("--serve-batch-workers", type=int, default=2, help="serving: batched-launch workers")
     args = ap.parse_args()
     if args.cpu_worker:
         cpu_worker(args)

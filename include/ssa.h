@@ -185,6 +185,26 @@ int ssa_decompose_batch(int nseries, const double* f, const int64_t* offsets, co
 /* Facts of series i: k, converged flag, thick restarts, products applied. */
 int ssa_batch_info(ssa_batch_t b, int i, int* k, int* converged, int* restarts, int64_t* matvecs);
 
+/*
+ * The same work split for repeated runs over series of unchanged sizes (a
+ * bootstrap, a stream of equally shaped batches):
+ *   ssa_batch_plan: validation, work order, twiddle tables, CTA slots and
+ *     outputs, once (no series data; all device memory is allocated here);
+ *   ssa_batch_run: one run on opts->stream for the series f (device memory,
+ *     or host memory copied into the batch's own buffer; pinned host memory
+ *     or device memory keeps the call capturable).  It only enqueues
+ *     memsets and the persistent kernel(s): no allocation, no host copy of
+ *     results and no synchronisation, so a CUDA graph can capture it;
+ *   ssa_batch_wait: waits for the last run and returns its status as
+ *     ssa_decompose_batch does.
+ * ssa_batch_get / ssa_batch_info / ssa_batch_reconstruct read the results
+ * of the last waited run.  Errors: as ssa_decompose_batch.
+ */
+int ssa_batch_plan(int nseries, const int64_t* offsets, const int64_t* Ls, const int32_t* ks, const ssa_opts_t* opts,
+                   ssa_batch_t* out);
+int ssa_batch_run(ssa_batch_t b, const double* f);
+int ssa_batch_wait(ssa_batch_t b);
+
 /* Results of series i: sigma (k), U (L x k), V (K x k), resid (k); NULL skips an output. */
 int ssa_batch_get(ssa_batch_t b, int i, double* sigma, double* U, double* V, double* resid);
 
@@ -244,7 +264,7 @@ typedef struct ssa_serve_opts {
   int precision;        /* SSA_PREC_F64 or SSA_PREC_F32C for every request (default SSA_PREC_F32C) */
   double tol;           /* as ssa_opts_t.tol (0 = the precision's default) */
   int64_t mem_budget;   /* device bytes that admitted requests may hold together (default 40 GiB) */
-  int workers;          /* single-series requests running at once (default 8, at most 64) */
+  int workers;          /* single-series requests running at once (default 16, at most 64) */
   int batch_workers;    /* batched launches running at once (default 2, at most 16; 0 = never batch) */
   int max_batch;        /* requests per batched launch (default 512) */
   int64_t batch_max_n;  /* only series with N <= this are batched (0 = the engine's limit, -1 = none) */
@@ -266,7 +286,7 @@ typedef struct ssa_serve_stats {
   int64_t batches, batched_requests;
 } ssa_serve_stats_t;
 
-/* Defaults: SSA_PREC_F32C, tol 0, 40 GiB, 8 workers, 2 batch workers, max_batch 512, batch_max_n 0. */
+/* Defaults: SSA_PREC_F32C, tol 0, 40 GiB, 16 workers, 2 batch workers, max_batch 512, batch_max_n 0. */
 void ssa_serve_default_opts(ssa_serve_opts_t* opts);
 /* Start the worker threads.  opts may be NULL (defaults).  Errors: SSA_EINVAL, SSA_ENOMEM. */
 int ssa_serve_create(const ssa_serve_opts_t* opts, ssa_server_t* out);

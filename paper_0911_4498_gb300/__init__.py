@@ -7,7 +7,8 @@ The compute lives in ``libssa_gb300.so`` (C ABI in ``include/ssa.h``);
 ``paper_0911_4498_gb300.build`` compiles it.  ``synth`` holds the seeded
 synthetic workloads.
 """
-from ._lib import (ssa_batch_destroy, ssa_batch_get, ssa_batch_info, ssa_batch_reconstruct, ssa_decompose_batch,  # noqa: F401
+from ._lib import (ssa_batch_destroy, ssa_batch_get, ssa_batch_info, ssa_batch_plan, ssa_batch_reconstruct,
+                   ssa_batch_run, ssa_batch_wait, ssa_decompose_batch,  # noqa: F401
                    SSA_ENOCONV, SSA_OK, SSA_PREC_F32C, SSA_PREC_F64, SSA_REFINE_OFF, SSA_REFINE_ON,
                    SSAError, groups_csr, lib, make_opts,
                    ssa_decomp_destroy, ssa_decomp_get, ssa_decomp_info, ssa_decompose, ssa_default_opts,

@@ -81,6 +81,9 @@ _SIGS = {
                             ctypes.POINTER(_I64)]),
     "ssa_batch_get": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "ssa_batch_reconstruct": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "ssa_batch_plan": (_I, [_I, _VP, _VP, _VP, ctypes.POINTER(SsaOpts), ctypes.POINTER(_VP)]),
+    "ssa_batch_run": (_I, [_VP, _VP]),
+    "ssa_batch_wait": (_I, [_VP]),
     "ssa_batch_destroy": (None, [_VP]),
     "ssa_hmatrix": (_I, [_VP, _I64, _I64, _I64, _I64, _VP, _I, ctypes.POINTER(SsaOpts), _VP]),
     "ssa_serve_default_opts": (None, [ctypes.POINTER(ServeOpts)]),
@@ -242,6 +245,22 @@ def ssa_batch_info(b, i: int):
 
 def ssa_batch_get(b, i: int, sigma=None, U=None, V=None, resid=None):
     _check(lib().ssa_batch_get(b, i, _ptr(sigma), _ptr(U), _ptr(V), _ptr(resid)))
+
+
+def ssa_batch_plan(offsets, Ls, ks, opts: SsaOpts | None = None):
+    """Batch plan for repeated runs (ssa_batch_run / ssa_batch_wait)."""
+    h = _VP()
+    _check(lib().ssa_batch_plan(len(Ls), _ptr(offsets, np.int64), _ptr(Ls, np.int64), _ptr(ks, np.int32),
+                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
+    return h
+
+
+def ssa_batch_run(b, f):
+    _check(lib().ssa_batch_run(b, _ptr(f)))
+
+
+def ssa_batch_wait(b) -> int:
+    return _check(lib().ssa_batch_wait(b), allow=(SSA_ENOCONV,))
 
 
 def ssa_batch_reconstruct(b, grp_off, grp_idx, m: int, out):

@@ -909,6 +909,18 @@ struct ssa_batch_s {
   cudaStream_t stream = nullptr;  // outputs are stream-ordered allocations on this stream
   int precision = SSA_PREC_F64;
   int lg_Mmax = 2;
+  // launch state kept for repeated runs (plan/run/wait): device tables, series
+  // table, work order, queue counters, per-series info, CTA slots
+  cplx<df64> *dtw = nullptr, *dA = nullptr, *dB = nullptr;
+  cplx<double> *dtw64 = nullptr, *dA64 = nullptr, *dB64 = nullptr;
+  BSeries* dser = nullptr;
+  int *dorder = nullptr, *dnext = nullptr, *dinfo = nullptr;
+  char* slots = nullptr;
+  double* fbuf = nullptr;  // device copy of host series
+  int64_t ftot = 0;
+  int nslots = 0;
+  bool refine = false;
+  BCtx cx{};
 };
 
 static int bfail(int code, const char* msg) {
@@ -957,11 +969,13 @@ static cplx<df64> b_tw(int64_t m, int64_t P) {
   return z;
 }
 
-extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* offsets, const int64_t* Ls,
-                                   const int32_t* ks, const ssa_opts_t* opts, ssa_batch_t* out) {
+// Validate the series, order them, build the twiddle tables and allocate
+// everything a run needs (no series data yet).
+static int batch_build(int nseries, const int64_t* offsets, const int64_t* Ls, const int32_t* ks,
+                       const ssa_opts_t* opts, ssa_batch_t* out) {
   if (!out) return bfail(SSA_EINVAL, "out is NULL");
   *out = nullptr;
-  if (nseries < 1 || !f || !offsets || !Ls || !ks) return bfail(SSA_EINVAL, "need nseries >= 1 and non-NULL arrays");
+  if (nseries < 1 || !offsets || !Ls || !ks) return bfail(SSA_EINVAL, "need nseries >= 1 and non-NULL arrays");
   ssa_opts_t o;
   if (opts) o = *opts;
   else ssa_default_opts(&o);
@@ -1063,95 +1077,70 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
   BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int nslots = std::min(sms, nseries);
   const int64_t sbytes = slot_bytes_for(ldu, ldv, nmax);
-  // device buffers
-  cplx<df64> *dtw = nullptr, *dA = nullptr, *dB = nullptr;
-  cplx<double> *dtw64 = nullptr, *dA64 = nullptr, *dB64 = nullptr;
-  BSeries* dser = nullptr;
-  int *dorder = nullptr, *dnext = nullptr, *dinfo = nullptr;
-  char* slots = nullptr;
-  double* fdev = nullptr;
-  bool own_f = false;
-  auto cleanup = [&]() {
-    if (dtw) cudaFreeAsync(dtw, s);
-    if (dA) cudaFreeAsync(dA, s);
-    if (dB) cudaFreeAsync(dB, s);
-    if (dtw64) cudaFreeAsync(dtw64, s);
-    if (dA64) cudaFreeAsync(dA64, s);
-    if (dB64) cudaFreeAsync(dB64, s);
-    if (dser) cudaFreeAsync(dser, s);
-    if (dorder) cudaFreeAsync(dorder, s);
-    if (dnext) cudaFreeAsync(dnext, s);
-    if (dinfo) cudaFreeAsync(dinfo, s);
-    if (slots) cudaFreeAsync(slots, s);
-    if (own_f && fdev) cudaFreeAsync(fdev, s);
-  };
+  // device buffers (owned by the batch)
 #define BCK2(x)                                                        \
   do {                                                                 \
     cudaError_t e_ = (x);                                              \
     if (e_ != cudaSuccess) {                                           \
       char m_[256];                                                    \
       std::snprintf(m_, sizeof m_, "%s: %s", #x, cudaGetErrorString(e_)); \
-      cleanup();                                                       \
       ssa_batch_destroy(b);                                            \
       return bfail(e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA, m_); \
     }                                                                  \
   } while (0)
-  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dtw), P * sizeof(cplx<df64>), s));
-  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dA), nA * sizeof(cplx<df64>), s));
-  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dB), nB * sizeof(cplx<df64>), s));
-  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dser), nseries * sizeof(BSeries), s));
-  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dorder), nseries * sizeof(int), s));
-  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dnext), 2 * sizeof(int), s));
-  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dinfo), 4 * (size_t)nseries * sizeof(int), s));
-  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&slots), (size_t)nslots * sbytes, s));
+  b->nslots = nslots;
+  b->refine = refine;
+  b->ftot = off[nseries];
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dtw), P * sizeof(cplx<df64>), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dA), nA * sizeof(cplx<df64>), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dB), nB * sizeof(cplx<df64>), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dser), nseries * sizeof(BSeries), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dorder), nseries * sizeof(int), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dnext), 2 * sizeof(int), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dinfo), 4 * (size_t)nseries * sizeof(int), s));
+  BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->slots), (size_t)nslots * sbytes, s));
   BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->U), std::max<int64_t>(b->totU, 1) * sizeof(double), s));
   BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->V), std::max<int64_t>(b->totV, 1) * sizeof(double), s));
   BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->sigma), std::max<int64_t>(b->totS, 1) * sizeof(double), s));
   BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->resid), std::max<int64_t>(b->totS, 1) * sizeof(double), s));
-  if (b_on_device(f)) {
-    fdev = const_cast<double*>(f);
-  } else {
-    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&fdev), off[nseries] * sizeof(double), s));
-    own_f = true;
-    BCK2(cudaMemcpyAsync(fdev, f, off[nseries] * sizeof(double), cudaMemcpyHostToDevice, s));
-  }
-  BCK2(cudaMemcpyAsync(dtw, htw.data(), P * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
-  BCK2(cudaMemcpyAsync(dA, hA.data(), nA * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
-  BCK2(cudaMemcpyAsync(dB, hB.data(), nB * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
-  BCK2(cudaMemcpyAsync(dser, b->ser.data(), nseries * sizeof(BSeries), cudaMemcpyHostToDevice, s));
-  BCK2(cudaMemcpyAsync(dorder, order.data(), nseries * sizeof(int), cudaMemcpyHostToDevice, s));
-  BCK2(cudaMemsetAsync(dnext, 0, 2 * sizeof(int), s));
+  BCK2(cudaMemcpyAsync(b->dtw, htw.data(), P * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
+  BCK2(cudaMemcpyAsync(b->dA, hA.data(), nA * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
+  BCK2(cudaMemcpyAsync(b->dB, hB.data(), nB * sizeof(cplx<df64>), cudaMemcpyHostToDevice, s));
+  BCK2(cudaMemcpyAsync(b->dser, b->ser.data(), nseries * sizeof(BSeries), cudaMemcpyHostToDevice, s));
+  BCK2(cudaMemcpyAsync(b->dorder, order.data(), nseries * sizeof(int), cudaMemcpyHostToDevice, s));
   if (refine) {
     std::vector<cplx<double>> h64(std::max(P, std::max(nA, nB)));
-    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dtw64), P * sizeof(cplx<double>), s));
-    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dA64), nA * sizeof(cplx<double>), s));
-    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&dB64), nB * sizeof(cplx<double>), s));
+    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dtw64), P * sizeof(cplx<double>), s));
+    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dA64), nA * sizeof(cplx<double>), s));
+    BCK2(cudaMallocAsync(reinterpret_cast<void**>(&b->dB64), nB * sizeof(cplx<double>), s));
     for (int64_t m = 0; m < P; ++m) h64[m] = b_tw64(m, P);
-    BCK2(cudaMemcpyAsync(dtw64, h64.data(), P * sizeof(cplx<double>), cudaMemcpyHostToDevice, s));
+    BCK2(cudaMemcpyAsync(b->dtw64, h64.data(), P * sizeof(cplx<double>), cudaMemcpyHostToDevice, s));
     for (int64_t m = 0; m < nA; ++m) h64[m] = b_tw64(m << tws, Mmax);
-    BCK2(cudaMemcpyAsync(dA64, h64.data(), nA * sizeof(cplx<double>), cudaMemcpyHostToDevice, s));
+    BCK2(cudaMemcpyAsync(b->dA64, h64.data(), nA * sizeof(cplx<double>), cudaMemcpyHostToDevice, s));
     for (int64_t m = 0; m < nB; ++m) h64[m] = b_tw64(m, Mmax);
-    BCK2(cudaMemcpyAsync(dB64, h64.data(), nB * sizeof(cplx<double>), cudaMemcpyHostToDevice, s));
+    BCK2(cudaMemcpyAsync(b->dB64, h64.data(), nB * sizeof(cplx<double>), cudaMemcpyHostToDevice, s));
   }
-  BCK2(cudaMemsetAsync(slots, 0, (size_t)nslots * sbytes, s));
-  BCtx cx{};
-  cx.ser = dser;
+  BCK2(cudaFuncSetAttribute(k_batch_ssa<float, 16384>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
+  BCK2(cudaFuncSetAttribute(k_batch_ssa<df64, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
+  BCK2(cudaFuncSetAttribute(k_batch_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
+  BCtx& cx = b->cx;
+  cx.ser = b->dser;
   cx.nseries = nseries;
-  cx.order = dorder;
-  cx.next = dnext;
-  cx.f = fdev;
+  cx.order = b->dorder;
+  cx.next = b->dnext;
+  cx.f = nullptr;
   cx.out_U = b->U;
   cx.out_V = b->V;
   cx.out_sigma = b->sigma;
   cx.out_resid = b->resid;
-  cx.out_info = dinfo;
-  cx.tw = dtw;
+  cx.out_info = b->dinfo;
+  cx.tw = b->dtw;
   cx.lg_P = lg_P;
-  cx.tA = dA;
-  cx.tB = dB;
+  cx.tA = b->dA;
+  cx.tB = b->dB;
   cx.tws = tws;
   cx.lg_Mmax = lgMmax;
-  cx.slots = slots;
+  cx.slots = b->slots;
   cx.slot_bytes = sbytes;
   cx.ldu = ldu;
   cx.ldv = ldv;
@@ -1160,41 +1149,99 @@ extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* 
   cx.tol = o.tol > 0 ? o.tol : (o.precision == SSA_PREC_F32C ? 1e-7 * std::sqrt((double)lgMmax) : 1e-12);
   cx.max_restarts = o.max_restarts;
   cx.seed = o.seed;
-  prof_begin(s);
-  if (o.precision == SSA_PREC_F32C) {
-    auto kern = k_batch_ssa<float, 16384>;
-    BCK2(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
-    kern<<<nslots, BT, B_SMEM, s>>>(cx);
-  } else {
-    auto kern = k_batch_ssa<df64, 8192>;
-    BCK2(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
-    kern<<<nslots, BT, B_SMEM, s>>>(cx);
-  }
-  prof_end(s, K_BATCH, 0.0, 0.0);
-  BCK2(cudaGetLastError());
-  if (refine) {
-    BRefine rf{dtw64, dA64, dB64, dnext + 1};
-    BCK2(cudaFuncSetAttribute(k_batch_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM));
-    prof_begin(s);
-    k_batch_refine<<<nslots, BT, B_SMEM, s>>>(cx, rf);
-    prof_end(s, K_BATCH, 0.0, 0.0);
-    BCK2(cudaGetLastError());
-  }
-  b->info.resize(4 * (size_t)nseries);
-  BCK2(cudaMemcpyAsync(b->info.data(), dinfo, 4 * (size_t)nseries * sizeof(int), cudaMemcpyDeviceToHost, s));
-  BCK2(cudaStreamSynchronize(s));
-  cleanup();
+  b->info.assign(4 * (size_t)nseries, 0);
 #undef BCK2
+  *out = b;
+  return SSA_OK;
+}
+
+// Enqueue one run on the batch's stream: queue counters, slots, the
+// persistent kernel (and the refinement).  Stream-ordered work only -- no
+// allocation, host copy or synchronisation -- so a CUDA graph can capture it.
+static int batch_enqueue(ssa_batch_t b, const double* fdev) {
+  cudaStream_t s = b->stream;
+  b->cx.f = fdev;
+  BCK(cudaMemsetAsync(b->dnext, 0, 2 * sizeof(int), s));
+  BCK(cudaMemsetAsync(b->slots, 0, (size_t)b->nslots * b->cx.slot_bytes, s));
+  prof_begin(s);
+  if (b->precision == SSA_PREC_F32C) k_batch_ssa<float, 16384><<<b->nslots, BT, B_SMEM, s>>>(b->cx);
+  else k_batch_ssa<df64, 8192><<<b->nslots, BT, B_SMEM, s>>>(b->cx);
+  prof_end(s, K_BATCH, 0.0, 0.0);
+  BCK(cudaGetLastError());
+  if (b->refine) {
+    BRefine rf{b->dtw64, b->dA64, b->dB64, b->dnext + 1};
+    prof_begin(s);
+    k_batch_refine<<<b->nslots, BT, B_SMEM, s>>>(b->cx, rf);
+    prof_end(s, K_BATCH, 0.0, 0.0);
+    BCK(cudaGetLastError());
+  }
+  return SSA_OK;
+}
+
+// Wait for the last run and read the per-series status.
+static int batch_finish(ssa_batch_t b) {
+  cudaStream_t s = b->stream;
+  BCK(cudaMemcpyAsync(b->info.data(), b->dinfo, b->info.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  BCK(cudaStreamSynchronize(s));
   int worst = SSA_OK;
-  for (int i = 0; i < nseries; ++i) {
+  for (int i = 0; i < b->nseries; ++i) {
     const unsigned st = (unsigned)b->info[4 * i + 3];
     if (st & SSA_DEV_NONFINITE) worst = SSA_ENUMERIC;
     else if (!b->info[4 * i] && worst == SSA_OK) worst = SSA_ENOCONV;
   }
-  *out = b;
   if (worst == SSA_ENUMERIC) host_set_error("non-finite value in a batched series");
   if (worst == SSA_ENOCONV) host_set_error("a batched series did not converge within max_restarts");
   return worst;
+}
+
+// series data for a run: device pointers are used in place; host data is
+// copied into the batch's own device buffer (pinned host memory keeps the
+// copy capturable)
+static int batch_input(ssa_batch_t b, const double* f, const double** fdev) {
+  if (b_on_device(f)) {
+    *fdev = f;
+    return SSA_OK;
+  }
+  if (!b->fbuf) BCK(cudaMallocAsync(reinterpret_cast<void**>(&b->fbuf), std::max<int64_t>(b->ftot, 1) * sizeof(double),
+                                    b->stream));
+  BCK(cudaMemcpyAsync(b->fbuf, f, b->ftot * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  *fdev = b->fbuf;
+  return SSA_OK;
+}
+
+extern "C" int ssa_decompose_batch(int nseries, const double* f, const int64_t* offsets, const int64_t* Ls,
+                                   const int32_t* ks, const ssa_opts_t* opts, ssa_batch_t* out) {
+  if (!f) return bfail(SSA_EINVAL, "f is NULL");
+  int rc = batch_build(nseries, offsets, Ls, ks, opts, out);
+  if (rc) return rc;
+  ssa_batch_t b = *out;
+  const double* fdev = nullptr;
+  rc = batch_input(b, f, &fdev);
+  if (!rc) rc = batch_enqueue(b, fdev);
+  if (rc) {
+    ssa_batch_destroy(b);
+    *out = nullptr;
+    return rc;
+  }
+  return batch_finish(b);
+}
+
+extern "C" int ssa_batch_plan(int nseries, const int64_t* offsets, const int64_t* Ls, const int32_t* ks,
+                              const ssa_opts_t* opts, ssa_batch_t* out) {
+  return batch_build(nseries, offsets, Ls, ks, opts, out);
+}
+
+extern "C" int ssa_batch_run(ssa_batch_t b, const double* f) {
+  if (!b || !f) return bfail(SSA_EINVAL, "NULL argument");
+  const double* fdev = nullptr;
+  int rc = batch_input(b, f, &fdev);
+  if (rc) return rc;
+  return batch_enqueue(b, fdev);
+}
+
+extern "C" int ssa_batch_wait(ssa_batch_t b) {
+  if (!b) return bfail(SSA_EINVAL, "NULL argument");
+  return batch_finish(b);
 }
 
 namespace ssa {
@@ -1335,7 +1382,9 @@ extern "C" int ssa_batch_get(ssa_batch_t b, int i, double* sigma, double* U, dou
 
 extern "C" void ssa_batch_destroy(ssa_batch_t b) {
   if (!b) return;
-  for (double* ptr : {b->U, b->V, b->sigma, b->resid})
+  void* bufs[] = {b->U, b->V, b->sigma, b->resid, b->dtw, b->dA, b->dB, b->dtw64, b->dA64, b->dB64,
+                  b->dser, b->dorder, b->dnext, b->dinfo, b->slots, b->fbuf};
+  for (void* ptr : bufs)
     if (ptr) cudaFreeAsync(ptr, b->stream);
   delete b;
 }

@@ -8,6 +8,18 @@
 
 namespace ssa {
 
+// Block-level end of a two-stage reduction: every block writes its partials,
+// the last block to finish sums them in block order (deterministic) and
+// resets the counter.
+SSA_D bool last_block(int* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  return is_last;
+}
+
 SSA_D df64 shfl_xor_df(df64 v, int m) {
   return make_df(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
 }

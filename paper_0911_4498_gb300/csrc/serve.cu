@@ -266,7 +266,7 @@ extern "C" void ssa_serve_default_opts(ssa_serve_opts_t* o) {
   o->precision = SSA_PREC_F32C;
   o->tol = 0.0;
   o->mem_budget = (int64_t)40 << 30;
-  o->workers = 8;
+  o->workers = 16;
   o->batch_workers = 2;
   o->max_batch = 512;
   o->batch_max_n = 0;

@@ -135,3 +135,76 @@ def test_batch_refinement_is_the_rayleigh_quotient(precision):
             assert ssa.ssa_batch_info(b, i)["matvecs"] > 0
     finally:
         ssa.ssa_batch_destroy(b)
+
+
+@pytest.mark.slow
+def test_full_size_batch_sampled():
+    """The 4096-series batch exactly as bench.py times it (F32C, one launch):
+    every series converges with sorted sigma, and sampled series match the oracle."""
+    fs, Ls, ks = synth.batch_workload(4096, seed=2)
+    off = np.zeros(len(fs) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([f.size for f in fs])
+    b, rc = ssa.ssa_decompose_batch(np.concatenate(fs), off, Ls.astype(np.int64), ks.astype(np.int32),
+                                    ssa.make_opts(precision=ssa.SSA_PREC_F32C))
+    try:
+        assert rc == ssa.SSA_OK
+        for i in range(len(fs)):
+            assert ssa.ssa_batch_info(b, i)["converged"]
+        for i in [0, 1, 777, 2048, 4095]:
+            sig = np.empty(int(ks[i]))
+            ssa.ssa_batch_get(b, i, sig, None, None, None)
+            assert np.all(np.diff(sig) <= 0)
+            ref = ossa.decompose(fs[i], int(Ls[i]), int(ks[i]), method="lanczos")
+            assert np.max(np.abs(sig - ref["sigma"]) / ref["sigma"]) <= 1e-5, i
+    finally:
+        ssa.ssa_batch_destroy(b)
+
+
+def test_plan_run_wait_and_cuda_graph_replay():
+    """ssa_batch_plan / ssa_batch_run / ssa_batch_wait give the results of
+    ssa_decompose_batch, and a run captured in a CUDA graph replays on new
+    series data in the same buffer."""
+    import torch
+    specs = [s for s in MIX if s[0] <= 16384]
+    Ns = [N for N, _, _ in specs]
+    off = np.zeros(len(specs) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(Ns)
+    Ls = np.array([L for _, L, _ in specs], dtype=np.int64)
+    ks = np.array([k for _, _, k in specs], dtype=np.int32)
+    fa = np.concatenate([synth.three_sines(N, seed=300 + i) for i, N in enumerate(Ns)])
+    fb = np.concatenate([synth.three_sines(N, seed=400 + i) for i, N in enumerate(Ns)])
+
+    def direct(f):
+        b, rc = ssa.ssa_decompose_batch(f, off, Ls, ks, ssa.make_opts(precision=ssa.SSA_PREC_F32C))
+        try:
+            return [_sig(b, i, k) for i, k in enumerate(ks)]
+        finally:
+            ssa.ssa_batch_destroy(b)
+
+    side = torch.cuda.Stream()
+    plan = ssa.ssa_batch_plan(off, Ls, ks, ssa.make_opts(precision=ssa.SSA_PREC_F32C, stream=side.cuda_stream))
+    try:
+        fd = torch.from_numpy(fa).cuda()
+        torch.cuda.synchronize()
+        ssa.ssa_batch_run(plan, fd)
+        assert ssa.ssa_batch_wait(plan) == ssa.SSA_OK
+        for got, ref in zip([_sig(plan, i, k) for i, k in enumerate(ks)], direct(fa)):
+            np.testing.assert_array_equal(got, ref)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side, capture_error_mode="relaxed"):
+            ssa.ssa_batch_run(plan, fd)
+        fd.copy_(torch.from_numpy(fb))
+        torch.cuda.synchronize()
+        g.replay()
+        side.synchronize()
+        assert ssa.ssa_batch_wait(plan) == ssa.SSA_OK
+        for got, ref in zip([_sig(plan, i, k) for i, k in enumerate(ks)], direct(fb)):
+            np.testing.assert_array_equal(got, ref)
+    finally:
+        ssa.ssa_batch_destroy(plan)
+
+
+def _sig(b, i, k):
+    out = np.empty(int(k))
+    ssa.ssa_batch_get(b, i, out, None, None, None)
+    return out

@@ -54,3 +54,23 @@ def test_rejects_bad_parameters():
                  (50, 100, 60, [52]), (50, 201, 60, [1])]:
         with pytest.raises(ssa.SSAError):
             ssa.ssa_hmatrix(f, *args)
+
+
+@pytest.mark.slow
+def test_full_size_sampled_rows():
+    """The section 6.4 timing setup as bench.py runs it (N = 4000, Q = N/2,
+    B = T = N/4, L = B/2, I = {1, 2}): sampled rows against the definition."""
+    from oracle import trajectory
+    N = 4000
+    B = T = N // 4
+    L = B // 2
+    f = synth.hmatrix_series(N, N // 2, seed=0)
+    G, rc = ssa.ssa_hmatrix(f, L, B, T, [1, 2])
+    assert rc == ssa.SSA_OK and G.shape == (N - B + 1, N - T + 1)
+    assert np.all(G >= 0) and np.all(G <= 1)
+    for i in (0, 1500, N - B):
+        U = ohm.base_vectors(f[i:i + B], L, [1, 2])
+        for j in range(0, N - T + 1, 211):
+            X = trajectory.trajectory_matrix(f[j:j + T], L)
+            R = X - U @ (U.T @ X)
+            assert abs(G[i, j] - np.sum(R * R) / np.sum(X * X)) <= 1e-9, (i, j)
