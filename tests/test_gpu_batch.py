@@ -195,8 +195,8 @@ def test_plan_run_wait_and_cuda_graph_replay():
             ssa.ssa_batch_run(plan, fd)
         fd.copy_(torch.from_numpy(fb))
         torch.cuda.synchronize()
-        g.replay()
-        side.synchronize()
+        g.replay()                 # launches on the current stream, not on the plan's stream
+        torch.cuda.synchronize()
         assert ssa.ssa_batch_wait(plan) == ssa.SSA_OK
         for got, ref in zip([_sig(plan, i, k) for i, k in enumerate(ks)], direct(fb)):
             np.testing.assert_array_equal(got, ref)
