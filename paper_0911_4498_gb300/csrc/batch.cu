@@ -129,13 +129,12 @@ int64_t batch_path_bytes(const std::vector<BatchItem>& items, int refine) {
     ldv = std::max(ldv, (Kw + 3) / 4 * 4);
     tot += (it.L + K) * it.k * 8 + it.k * 16 + it.N * 8 + (int64_t)sizeof(BSeries) + 24;
   }
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {  // thread-safe one-time initialisation
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms < 1) sms = 152;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 152;
+  }();
   const int64_t nslots = std::min<int64_t>(sms, (int64_t)items.size());
   tot += nslots * slot_bytes_for(ldu, ldv, nmax);
   tot += (Mmax / 2 + 2 * Mmax) * 16 * (refine ? 2 : 1);  // twiddle tables

@@ -2,6 +2,7 @@
 // classical Gram-Schmidt: the tile-walking passes over the basis, their
 // reductions with the Kahan-Parlett gate of the third pass, the wide-basis
 // fallback passes, and the launcher.  All vectors are double-float (df64).
+#include <mutex>
 #include "lanczos.h"
 #include "lanczos_dev.cuh"
 #include "prof.h"
@@ -406,15 +407,19 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
   prof_end(s, K_UPDATE, qb + 16.0 * dim, fl);
 }
 
+// kernel attributes and the SM count, once per process (plans are created from many threads)
+static std::once_flag g_reorth_once;
 static int g_sms = 0;
 void reorth_setup() {
-  const int mx = (int)(((size_t)NST * (FUSED_MAXCOL * FRP + FR) + FUSED_MAXCOL) * sizeof(df64));
-  cudaFuncSetAttribute(k_cgs_tiles<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_cgs_tiles<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_cgs_tiles<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  std::call_once(g_reorth_once, [] {
+    const int mx = (int)(((size_t)NST * (FUSED_MAXCOL * FRP + FR) + FUSED_MAXCOL) * sizeof(df64));
+    cudaFuncSetAttribute(k_cgs_tiles<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_cgs_tiles<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_cgs_tiles<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  });
 }
 // persistent grid of the fused pass: as many blocks as fit on every SM at once
 int fused_grid(size_t smem_bytes) {

@@ -268,7 +268,8 @@ struct ssa_decomp_s {
 namespace ssa {
 static const char* const kClassNames[K_NCLASS] = {
     "spectrum", "matvec_small", "matvec_colfwd", "matvec_row", "matvec_colinv", "cgs_proj", "cgs_update",
-    "cgs_update_proj", "normalize", "small_svd", "svd_precondition", "ritz", "hankel_small", "hankel_fourstep", "misc", "gated", "batch_ssa"};
+    "cgs_update_proj", "normalize", "small_svd", "svd_precondition", "ritz", "hankel_small", "hankel_fourstep",
+    "misc", "gated", "batch_ssa"};
 struct PendingLaunch {
   int cls;
   cudaEvent_t a, b;

@@ -5,6 +5,7 @@
 // restart, and the output conversion with the sign rule.  All vectors and the
 // projected problem are double-float (df64).
 #include <cooperative_groups.h>
+#include <mutex>
 #include "lanczos.h"
 #include "lanczos_dev.cuh"
 #include "prof.h"
@@ -600,18 +601,17 @@ void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* be
   prof_end(s, mode == 0 ? K_NORMALIZE : K_GATED, mode == 0 ? 16.0 * dim : 0.0, 0.0);
 }
 
-static int g_coop_blocks = 0;
 int coop_blocks() {
-  if (g_coop_blocks == 0) {
+  static const int blocks = [] {  // thread-safe one-time initialisation
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_normalize_coop, 256, 0);
     if (per < 1) per = 1;
     if (per > 4) per = 4;
-    g_coop_blocks = sms * per;
-  }
-  return g_coop_blocks;
+    return sms * per;
+  }();
+  return blocks;
 }
 
 int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est,
@@ -642,22 +642,21 @@ void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, 
   const int nloc_p = (c + SVD_CL - 1) / SVD_CL;
   const size_t pre_cl_sm = (size_t)nloc_p * (r + c) * sizeof(float);
   if (c >= 16 && pre_cl_sm <= (size_t)PRE_SMEM_MAX) {
-    static bool attr_c = false;
-    if (!attr_c) {
-      cudaFuncSetAttribute(k_svd_precondition_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, PRE_SMEM_MAX);
-      attr_c = true;
-    }
+    static std::once_flag attr_c;
+    std::call_once(attr_c, [] {
+      cudaFuncSetAttribute(k_svd_precondition_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           PRE_SMEM_MAX);
+    });
     prof_begin(s);
     k_svd_precondition_cluster<<<SVD_CL, SVD_CL_THREADS, pre_cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc,
                                                                          PRE_SWEEPS, 2e-6f);
     prof_end(s, K_SVD_PRE, 0.0, 0.0);
     warm = 1;
   } else if (c >= 16 && pre_sm <= (size_t)PRE_SMEM_MAX) {
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [] {
       cudaFuncSetAttribute(k_svd_precondition, cudaFuncAttributeMaxDynamicSharedMemorySize, PRE_SMEM_MAX);
-      attr = true;
-    }
+    });
     prof_begin(s);
     // FP32 sweeps stop improving near FP32 resolution; the df64 sweeps finish from there
     k_svd_precondition<<<1, PRE_THREADS, pre_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc, PRE_SWEEPS, 2e-6f);
@@ -668,11 +667,10 @@ void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, 
   const int nloc = (c + SVD_CL - 1) / SVD_CL;
   const size_t cl_sm = ((size_t)nloc * (r + c) + nloc) * sizeof(df64);
   if (cl_sm <= (size_t)SVD_STAGE_MAX) {
-    static bool attr3 = false;
-    if (!attr3) {
+    static std::once_flag attr3;
+    std::call_once(attr3, [] {
       cudaFuncSetAttribute(k_small_svd_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, SVD_STAGE_MAX);
-      attr3 = true;
-    }
+    });
     prof_begin(s);
     k_small_svd_cluster<<<SVD_CL, SVD_CL_THREADS, cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, cc, sw.sigma, sw.P, sw.Q,
                                                                sw.resid, sw.sigma_d, k, tol_conv, sw.conv, est,
@@ -682,11 +680,10 @@ void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, 
   }
   const size_t st_sm = ((size_t)r * c + (size_t)c * c) * sizeof(df64);
   const int staged = st_sm <= (size_t)SVD_STAGE_MAX ? 1 : 0;
-  static bool attr2 = false;
-  if (!attr2) {
+  static std::once_flag attr2;
+  std::call_once(attr2, [] {
     cudaFuncSetAttribute(k_small_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, SVD_STAGE_MAX);
-    attr2 = true;
-  }
+  });
   prof_begin(s);
   k_small_svd<<<1, SVD_THREADS, staged ? st_sm : 0, s>>>(B, ldb, r, c, sw.A, sw.W, cc, sw.sigma, sw.P, sw.Q,
                                                          sw.resid, sw.sigma_d, k, tol_conv, sw.conv, est, status,
@@ -705,11 +702,11 @@ void launch_ritz(const df64* Q, int64_t ldq, int r, const df64* P, int ldp, int 
                  int64_t dim, cudaStream_t s) {
   dim3 grid((unsigned)((dim + 63) / 64), (unsigned)((ncol + 31) / 32));
   const size_t sm = (size_t)r * 32 * sizeof(df64);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(MAXCOL + 2) * 32 * 8);
-    attr = true;
-  }
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(MAXCOL + 2) * 32 * 8);
+  });
   prof_begin(s);
   k_ritz<<<grid, 256, sm, s>>>(Q, ldq, r, P, ldp, ncol, out, ldo, dim);
   prof_end(s, K_RITZ, 8.0 * (double)dim * (r + ncol), 2.0 * (double)dim * r * ncol);
