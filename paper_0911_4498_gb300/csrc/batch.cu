@@ -32,6 +32,7 @@ constexpr int B_MAXD = 72;              // largest Krylov dimension of a batched
 constexpr int B_MAXC = B_MAXD + 2;      // basis columns / projected-matrix size
 constexpr int B_FR = 64;                // CGS tile rows
 constexpr int B_FRP = 66;               // CGS tile column stride
+constexpr int B_NST = 3;                // CGS pipeline stages: 3 x (73 x 66 + 64) df64 fit the 128 KB buffer
 
 struct BSeries {
   int64_t f_off, N, L, K;  // user sizes
@@ -265,13 +266,17 @@ SSA_D void cta_cgs_pass(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t 
   };
   dacc acc = dacc_zero();
   df64 nrm = df_zero();
-  issue(0, 0);
-  cp_async_commit();
-  for (int tile = 0; tile < ntiles; ++tile) {
-    const int stage = tile & 1;
-    if (tile + 1 < ntiles) issue(stage ^ 1, tile + 1);
+  // B_NST-stage pipeline: tiles tile+1 .. tile+B_NST-1 are in flight while tile is processed
+  for (int p = 0; p < B_NST - 1; ++p) {
+    if (p < ntiles) issue(p, p);
     cp_async_commit();
-    cp_async_wait<1>();
+  }
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int stage = tile % B_NST;
+    const int ahead = tile + B_NST - 1;
+    if (ahead < ntiles) issue(ahead % B_NST, ahead);
+    cp_async_commit();
+    cp_async_wait<B_NST - 1>();
     __syncthreads();
     const df64* Qs = stbuf + stage * stage_elems;
     df64* ws = const_cast<df64*>(Qs) + ncols * B_FRP;
