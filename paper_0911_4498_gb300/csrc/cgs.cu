@@ -1,5 +1,5 @@
 // Reorthogonalisation against the Lanczos basis (section 3.2.2) by
-// classical Gram-Schmidt: the tile-walking passes over the basis, their
+// classical Gram-Schmidt: the fused lane-owned passes over the basis, their
 // reductions with the Kahan-Parlett gate of the third pass, the wide-basis
 // fallback passes, and the launcher.  All vectors are double-float (df64).
 #include <mutex>
@@ -104,148 +104,165 @@ __global__ void k_reduce_gate(const df64* __restrict__ part, int ntiles, int ldp
   }
 }
 
-// Tile-walking CGS pass over Q (dim x ncols, ncols <= FUSED_MAXCOL):
+// Fused CGS pass over Q (dim x ncols column-major, ncols <= 8 * CPW):
 //   UPD:  w <- w - Q h          (h read from memory)
 //   PROJ: part[block][c] = sum over the block's tiles of Q[tile, c] . w[tile]
-//   always: part[block][ncols] = sum of w.w over the block's tiles (after UPD)
-// Persistent blocks walk tiles of FR rows; every thread copies its share of
-// the next tile (all columns and the w rows) to shared memory with 16-byte
-// asynchronous copies while the current tile is processed (double buffer).
-// The compute threads read two rows at a time (128-bit shared loads) and
-// accumulate with a 12-instruction double-float multiply-add.  (One-thread
-// bulk copies of the 512-byte column segments measured slower: the copy
-// engine serialises many small requests.)
-constexpr int FR = 64;   // rows per tile
-constexpr int FRP = 66;  // column stride in shared memory (16-byte aligned)
-constexpr int NST = 2;   // pipeline stages (tiles in shared memory per block); 32-row tiles with
-                         // 4 stages measured slower (more per-tile overhead)
-template <bool UPD, bool PROJ>
-__global__ void __launch_bounds__(256) k_cgs_tiles(const df64* __restrict__ Q, int64_t ldq, int ncols,
-                                                   df64* __restrict__ w, int64_t dim, const df64* __restrict__ h,
-                                                   df64* __restrict__ part, int ldp, int ntiles, const int* flag,
-                                                   unsigned* status) {
+//   always: part[block][ncols] = w.w over the block's tiles (after UPD)
+// Persistent blocks walk tiles of 64 rows.  Warp wp owns the columns
+// c = wp + 8m (m < CPW) and lane l the rows 2l, 2l+1 of every tile, so each
+// lane stages (16-byte cp.async, NST tiles deep) and reads back only the
+// pieces it copied itself: the basis tiles need no barrier.  (Requesting
+// tiles further ahead into L2 with bulk prefetches measured slower in every
+// pass.)  Under UPD every warp forms
+// the partial row sums Q[rows, its columns] h[its columns]; after one barrier
+// the first 64 threads add the eight partials of their row in warp order and
+// write x = w - Q h (to shared memory when PROJ follows, and to w).  Under
+// PROJ every lane accumulates its columns' products with its two rows of x
+// over all the block's tiles in registers (lazy double-float accumulators);
+// one warp reduction per column at the end.  Rows of w are prefetched into
+// registers one tile ahead.  The projection after an update needs one more
+// barrier (x visible); update-only passes double-buffer the partials instead.
+constexpr int LR = 64;  // rows per tile: 32 lanes x 2 rows
+template <bool UPD, bool PROJ, int CPW, int NST>
+__global__ void __launch_bounds__(256, (CPW <= 13 ? 2 : 1))
+    k_cgs_lanes(const df64* __restrict__ Q, int64_t ldq, int ncols, df64* __restrict__ w, int64_t dim,
+                const df64* __restrict__ h, df64* __restrict__ part, int ldp, int ntiles, const int* flag) {
   if (flag && *flag == 0) return;
+  constexpr int NRED = (UPD && !PROJ) ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ df64 red[8];
-  const int stage_elems = ncols * FRP + FR;
+  __shared__ __align__(16) df64 red[NRED][8][LR];
+  __shared__ __align__(16) df64 xs[LR];
+  __shared__ df64 nred[8];
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   df64* st0 = reinterpret_cast<df64*>(smem_raw);
-  df64* hs = st0 + NST * stage_elems;
-  const int tid = threadIdx.x;
-  if (UPD)
-    for (int c = tid; c < ncols; c += 256) hs[c] = h[c];
-  auto issue = [&](int stg, int tile) {  // all threads: 16-byte asynchronous copies
-    const int64_t r0 = (int64_t)tile * FR;
-    df64* st = st0 + stg * stage_elems;
-    for (int e = tid; e < (ncols + 1) * (FR / 2); e += 256) {
-      const int c = e / (FR / 2), l = e - c * (FR / 2);
-      const int64_t row = r0 + 2 * l;
-      const bool ok = row < dim;
-      if (c < ncols)
-        cp_async16(st + c * FRP + 2 * l, ok ? (const void*)(Q + (int64_t)c * ldq + row) : (const void*)Q, ok);
-      else
-        cp_async16(st + ncols * FRP + 2 * l, ok ? (const void*)(w + row) : (const void*)w, ok);
-    }
+  const int stage_elems = ncols * LR;
+  df64 hr[CPW];
+  dacc acc[CPW];
+#pragma unroll
+  for (int m = 0; m < CPW; ++m) {
+    const int c = wp + 8 * m;
+    hr[m] = (UPD && c < ncols) ? h[c] : df_zero();
+    acc[m] = dacc_zero();
+  }
+  dacc nacc = dacc_zero();
+  const df64* qlane = Q + (int64_t)wp * ldq + 2 * lane;
+  const int64_t qstep = 8 * ldq;
+  auto issue = [&](int stg, int tile) {  // this lane's 16-byte pieces of the tile (column c at c * LR)
+    df64* st = st0 + stg * stage_elems + wp * LR + 2 * lane;
+    const int64_t r0 = (int64_t)tile * LR;
+    const bool ok = r0 + 2 * lane < dim;
+#pragma unroll
+    for (int m = 0; m < CPW; ++m)
+      if (wp + 8 * m < ncols)
+        cp_async16(st + 8 * m * LR, ok ? (const void*)(qlane + m * qstep + r0) : (const void*)Q, ok);
   };
-  dacc acc0 = dacc_zero(), acc1 = dacc_zero();
-  df64 nrm = df_zero();
-  // prologue: the first NST-1 tiles of this block in flight
+  // rows of w: under UPD the first 64 threads hold one row each (plain loads: w is written
+  // by this pass); otherwise every lane holds its two rows (read-only path)
+  auto wrow = [&](int tile) -> df64 {
+    const int64_t row = (int64_t)tile * LR + tid;
+    return row < dim ? w[row] : df_zero();
+  };
+  auto wpair = [&](int tile) -> float4 { return ld_pair(w, (int64_t)tile * LR + 2 * lane, dim); };
   for (int p = 0; p < NST - 1; ++p) {
     const int t = blockIdx.x + p * gridDim.x;
     if (t < ntiles) issue(p, t);
     cp_async_commit();
   }
+  df64 wr = df_zero();
+  float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (blockIdx.x < ntiles) {
+    if (UPD) {
+      if (tid < LR) wr = wrow(blockIdx.x);
+    } else {
+      wv = wpair(blockIdx.x);
+    }
+  }
   int it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int stage = it % NST;
     const int ahead = tile + (NST - 1) * gridDim.x;
     if (ahead < ntiles) issue((it + NST - 1) % NST, ahead);
     cp_async_commit();
-    cp_async_wait<NST - 1>();
-    __syncthreads();
-    const df64* Qs = st0 + stage * stage_elems;
-    df64* ws = const_cast<df64*>(Qs) + ncols * FRP;
-    const int64_t r0 = (int64_t)tile * FR;
-    {  // rows 2rp, 2rp+1 of w (updated when UPD); 8 threads per row pair split the columns
-      const int rp = tid >> 3, q = tid & 7;
-      dacc a0 = dacc_zero(), a1 = dacc_zero();
+    const int nxt = tile + gridDim.x;
+    df64 wr_n = wr;
+    float4 wv_n = wv;
+    if (nxt < ntiles) {
       if (UPD) {
-        for (int c = q; c < ncols; c += 8) {
-          const float4 v = *reinterpret_cast<const float4*>(Qs + c * FRP + 2 * rp);
-          const df64 hc = hs[c];
-          dacc_fma(a0, make_df(v.x, v.y), hc);
-          dacc_fma(a1, make_df(v.z, v.w), hc);
-        }
+        if (tid < LR) wr_n = wrow(nxt);
+      } else {
+        wv_n = wpair(nxt);
       }
-      df64 s0 = dacc_val(a0), s1 = dacc_val(a1);
+    }
+    cp_async_wait<NST - 1>();
+    const df64* sl = st0 + (it % NST) * stage_elems + wp * LR + 2 * lane;
+    const int64_t r0 = (int64_t)tile * LR;
+    if (UPD) {
+      dacc a0 = dacc_zero(), a1 = dacc_zero();
 #pragma unroll
-      for (int m = 1; m < 8; m <<= 1) {
-        s0 = df_add(s0, shfl_xor_df(s0, m));
-        s1 = df_add(s1, shfl_xor_df(s1, m));
+      for (int m = 0; m < CPW; ++m) {
+        if (wp + 8 * m < ncols) {
+          const float4 v = *reinterpret_cast<const float4*>(sl + 8 * m * LR);
+          dacc_fma(a0, make_df(v.x, v.y), hr[m]);
+          dacc_fma(a1, make_df(v.z, v.w), hr[m]);
+        }
       }
+      const df64 s0 = dacc_val(a0), s1 = dacc_val(a1);
+      df64(*rb)[LR] = red[NRED == 2 ? (it & 1) : 0];
+      *reinterpret_cast<float4*>(&rb[wp][2 * lane]) = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
       __syncthreads();
-      if (q == 0) {
-        const int64_t g0 = r0 + 2 * rp;
-        const df64 x0 = g0 < dim ? df_sub(ws[2 * rp], s0) : df_zero();
-        const df64 x1 = g0 + 1 < dim ? df_sub(ws[2 * rp + 1], s1) : df_zero();
-        ws[2 * rp] = x0;
-        ws[2 * rp + 1] = x1;
-        if (UPD) {
-          if (g0 < dim) w[g0] = x0;
-          if (g0 + 1 < dim) w[g0 + 1] = x1;
+      if (tid < LR) {
+        df64 s = rb[0][tid];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) s = df_add(s, rb[q][tid]);
+        const int64_t row = r0 + tid;
+        const df64 x = row < dim ? df_sub(wr, s) : df_zero();
+        if (PROJ) xs[tid] = x;
+        if (row < dim) w[row] = x;
+        dacc_fma(nacc, x, x);
+      }
+      if (PROJ) __syncthreads();
+    }
+    if (PROJ) {
+      const float4 xv = UPD ? *reinterpret_cast<const float4*>(&xs[2 * lane]) : wv;
+      const df64 x0 = make_df(xv.x, xv.y), x1 = make_df(xv.z, xv.w);
+      if (!UPD && wp == 0) {
+        dacc_fma(nacc, x0, x0);
+        dacc_fma(nacc, x1, x1);
+      }
+#pragma unroll
+      for (int m = 0; m < CPW; ++m) {
+        if (wp + 8 * m < ncols) {
+          const float4 v = *reinterpret_cast<const float4*>(sl + 8 * m * LR);
+          dacc_fma(acc[m], make_df(v.x, v.y), x0);
+          dacc_fma(acc[m], make_df(v.z, v.w), x1);
         }
-        if (!PROJ) {
-          nrm = df_fma(x0, x0, nrm);
-          nrm = df_fma(x1, x1, nrm);
-        }
+      }
+      if ((it & 15) == 15) {
+#pragma unroll
+        for (int m = 0; m < CPW; ++m) dacc_norm(acc[m]);
       }
     }
-    __syncthreads();
-    if (PROJ) {  // two threads per column (one per half tile); column ncols is w.w
-      const int half = tid & 1;
-      const int c = tid >> 1, c1 = (tid + 256) >> 1;
-      const float4* wv = reinterpret_cast<const float4*>(ws + half * (FR / 2));
-      if (c <= ncols) {
-        const float4* col = reinterpret_cast<const float4*>((c < ncols ? Qs + c * FRP : ws) + half * (FR / 2));
-#pragma unroll 4
-        for (int i = 0; i < FR / 4; ++i) {
-          const float4 qv = col[i], xv = wv[i];
-          dacc_fma(acc0, make_df(qv.x, qv.y), make_df(xv.x, xv.y));
-          dacc_fma(acc0, make_df(qv.z, qv.w), make_df(xv.z, xv.w));
-        }
-        dacc_norm(acc0);
-      }
-      if (c1 <= ncols) {
-        const float4* col = reinterpret_cast<const float4*>((c1 < ncols ? Qs + c1 * FRP : ws) + half * (FR / 2));
-#pragma unroll 4
-        for (int i = 0; i < FR / 4; ++i) {
-          const float4 qv = col[i], xv = wv[i];
-          dacc_fma(acc1, make_df(qv.x, qv.y), make_df(xv.x, xv.y));
-          dacc_fma(acc1, make_df(qv.z, qv.w), make_df(xv.z, xv.w));
-        }
-        dacc_norm(acc1);
-      }
-    }
-    __syncthreads();
+    wr = wr_n;
+    wv = wv_n;
   }
   cp_async_wait<0>();
+  df64 nv = warp_sum_df(dacc_val(nacc));
+  if (lane == 0) nred[wp] = nv;
   if (PROJ) {
-    df64 v0 = dacc_val(acc0), v1 = dacc_val(acc1);
-    v0 = df_add(v0, shfl_xor_df(v0, 1));
-    v1 = df_add(v1, shfl_xor_df(v1, 1));
-    const int c = tid >> 1, c1 = (tid + 256) >> 1;
-    if ((tid & 1) == 0) {
-      if (c <= ncols) part[(int64_t)blockIdx.x * ldp + c] = v0;
-      if (c1 <= ncols) part[(int64_t)blockIdx.x * ldp + c1] = v1;
+#pragma unroll
+    for (int m = 0; m < CPW; ++m) {
+      const int c = wp + 8 * m;
+      if (c < ncols) {  // warp-uniform
+        const df64 v = warp_sum_df(dacc_val(acc[m]));
+        if (lane == 0) part[(int64_t)blockIdx.x * ldp + c] = v;
+      }
     }
-  } else {
-    nrm = warp_sum_df(nrm);
-    if ((tid & 31) == 0) red[tid >> 5] = nrm;
-    __syncthreads();
-    if (tid == 0) {
-      df64 t = df_zero();
-      for (int i = 0; i < 8; ++i) t = df_add(t, red[i]);
-      part[(int64_t)blockIdx.x * ldp + ncols] = t;
-    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    df64 t = nred[0];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t = df_add(t, nred[q]);
+    part[(int64_t)blockIdx.x * ldp + ncols] = t;
   }
 }
 
@@ -338,9 +355,29 @@ __global__ void __launch_bounds__(RT) k_cgs_update(const df64* __restrict__ Q, i
 
 
 // ---------------------------------------------------------------- launchers
+constexpr int LNST = 2;  // staged tiles per block: two blocks per SM fit bases up to ~104 columns
 int reorth_blocks(int64_t dim) { return (int)((dim + SLAB - 1) / SLAB); }
-int fused_tiles(int64_t dim) { return (int)((dim + FR - 1) / FR); }
-int fused_grid(size_t smem_bytes);
+int fused_tiles(int64_t dim) { return (int)((dim + LR - 1) / LR); }
+
+// persistent grid of the fused passes per [pass][ncols]: as many blocks as fit on every SM at once
+enum { P_PROJ = 0, P_UPD_PROJ = 1, P_UPD = 2 };
+static int g_lanes_grid[3][FUSED_MAXCOL + 1];
+static int g_sms = 0;
+
+template <bool UPD, bool PROJ, int CPW>
+static void lanes_one(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, const df64* h, df64* part,
+                      int ldp, int G, int T, const int* flag, cudaStream_t s) {
+  const size_t sm = (size_t)LNST * ncols * LR * sizeof(df64);
+  k_cgs_lanes<UPD, PROJ, CPW, LNST><<<G, 256, sm, s>>>(Q, ldq, ncols, w, dim, h, part, ldp, T, flag);
+}
+template <bool UPD, bool PROJ>
+static void lanes_pass(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, const df64* h, df64* part,
+                       int ldp, int G, int T, const int* flag, cudaStream_t s) {
+  if (ncols <= 32) lanes_one<UPD, PROJ, 4>(Q, ldq, ncols, w, dim, h, part, ldp, G, T, flag, s);
+  else if (ncols <= 64) lanes_one<UPD, PROJ, 8>(Q, ldq, ncols, w, dim, h, part, ldp, G, T, flag, s);
+  else if (ncols <= 104) lanes_one<UPD, PROJ, 13>(Q, ldq, ncols, w, dim, h, part, ldp, G, T, flag, s);
+  else lanes_one<UPD, PROJ, 25>(Q, ldq, ncols, w, dim, h, part, ldp, G, T, flag, s);
+}
 
 void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, int mode,
                  cudaStream_t s) {
@@ -351,23 +388,24 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
   const int* flag = nullptr;
   if (ncols <= FUSED_MAXCOL) {
     const int T2 = fused_tiles(dim);
-    const size_t sm = ((size_t)NST * (ncols * FRP + FR) + ncols) * sizeof(df64);
-    const int G2 = T2 < fused_grid(sm) ? T2 : fused_grid(sm);
+    auto grid = [&](int pass) { return g_lanes_grid[pass][ncols] < T2 ? g_lanes_grid[pass][ncols] : T2; };
     const int ldp = rw.ldp2;
     const df64* hlast = rw.h;
     const int* gate = nullptr;
     if (ncols > 0) {
       // pass 1: h = Q^T w and ||w||^2 (column ncols)
+      const int G1 = grid(P_PROJ);
       prof_begin(s);
-      k_cgs_tiles<false, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag, rw.status);
+      lanes_pass<false, true>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, G1, T2, flag, s);
       prof_end(s, K_PROJ, qb + 8.0 * dim, fl);
       prof_begin(s);
-      k_reduce_cols<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols + 1, rw.h, flag);
+      k_reduce_cols<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G1, ldp, ncols + 1, rw.h, flag);
       prof_end(s, K_MISC, 0.0, 0.0);
       if (mode == REORTH_GATED) {
         // pass 2: w <- w - Q h, h2 = Q^T w, ||w||^2; the gate decides on pass 3
+        const int G2 = grid(P_UPD_PROJ);
         prof_begin(s);
-        k_cgs_tiles<true, true><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, T2, flag, rw.status);
+        lanes_pass<true, true>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, G2, T2, flag, s);
         prof_end(s, K_UPDATE_PROJ, qb + 16.0 * dim, 2 * fl);
         prof_begin(s);
         k_reduce_gate<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols, rw.h2, rw.h + ncols, rw.gate,
@@ -378,11 +416,12 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
       }
     }
     // last pass: w <- w - Q h, ||w||^2 (skipped on the device when the gate is 0)
+    const int G3 = grid(P_UPD);
     prof_begin(s);
-    k_cgs_tiles<true, false><<<G2, 256, sm, s>>>(Q, ldq, ncols, w, dim, hlast, rw.part2, ldp, T2, gate, rw.status);
+    lanes_pass<true, false>(Q, ldq, ncols, w, dim, hlast, rw.part2, ldp, G3, T2, gate, s);
     prof_end(s, gate ? K_GATED : K_UPDATE, gate ? 0.0 : qb + 16.0 * dim, gate ? 0.0 : fl);
     prof_begin(s);
-    k_reduce_one<<<1, 32, 0, s>>>(rw.part2, G2, ldp, ncols, rw.nrm, gate);
+    k_reduce_one<<<1, 32, 0, s>>>(rw.part2, G3, ldp, ncols, rw.nrm, gate);
     prof_end(s, K_MISC, 0.0, 0.0);
     return;
   }
@@ -407,26 +446,36 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
   prof_end(s, K_UPDATE, qb + 16.0 * dim, fl);
 }
 
-// kernel attributes and the SM count, once per process (plans are created from many threads)
+// kernel attributes, the SM count and the grid table, once per process (plans are created
+// from many threads)
+template <bool UPD, bool PROJ, int CPW>
+static void lanes_setup_one(int pass, int lo, int hi) {
+  auto fn = k_cgs_lanes<UPD, PROJ, CPW, LNST>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(LNST * 8 * CPW * LR * sizeof(df64)));
+  for (int n = lo; n <= hi; ++n) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, (size_t)LNST * n * LR * sizeof(df64));
+    g_lanes_grid[pass][n] = (g_sms > 0 ? g_sms : 152) * (per < 1 ? 1 : per);
+  }
+}
+template <bool UPD, bool PROJ>
+static void lanes_setup(int pass) {
+  lanes_setup_one<UPD, PROJ, 4>(pass, 0, 32);
+  lanes_setup_one<UPD, PROJ, 8>(pass, 33, 64);
+  lanes_setup_one<UPD, PROJ, 13>(pass, 65, 104);
+  lanes_setup_one<UPD, PROJ, 25>(pass, 105, FUSED_MAXCOL);
+}
+static_assert(FUSED_MAXCOL <= 8 * 25, "fused passes hold at most 25 columns per warp");
 static std::once_flag g_reorth_once;
-static int g_sms = 0;
 void reorth_setup() {
   std::call_once(g_reorth_once, [] {
-    const int mx = (int)(((size_t)NST * (FUSED_MAXCOL * FRP + FR) + FUSED_MAXCOL) * sizeof(df64));
-    cudaFuncSetAttribute(k_cgs_tiles<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_cgs_tiles<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_cgs_tiles<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    lanes_setup<false, true>(P_PROJ);
+    lanes_setup<true, true>(P_UPD_PROJ);
+    lanes_setup<true, false>(P_UPD);
   });
-}
-// persistent grid of the fused pass: as many blocks as fit on every SM at once
-int fused_grid(size_t smem_bytes) {
-  int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgs_tiles<true, true>, 256, smem_bytes);
-  if (per < 1) per = 1;
-  return (g_sms > 0 ? g_sms : 152) * per;
 }
 
 }  // namespace ssa
