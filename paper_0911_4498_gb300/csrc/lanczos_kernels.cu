@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_small_svd(const df64* __restric
 // svd_jacobi_body (same order, same reductions), so the results are the
 // same bit for bit; the work of a round is spread over SVD_CL SMs instead of
 // one.
+template <int NPL>
 __global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
     k_small_svd_cluster(const df64* __restrict__ B, int ldb, int r, int c, const df64* __restrict__ Ain,
                         const df64* __restrict__ Win, int cc, df64* __restrict__ sigma, df64* __restrict__ P,
@@ -215,12 +216,35 @@ __global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
         if (p >= c || q >= c) continue;
         df64* ap = colA(p);
         df64* aq = colA(q);
+        df64* wp = colW(p);
+        df64* wq = colW(q);
         df64 al = df_zero(), be = df_zero(), ga = df_zero();
-        for (int i = lane; i < r; i += 32) {
-          const df64 x = ap[i], y = aq[i];
-          al = df_fma(x, x, al);
-          be = df_fma(y, y, be);
-          ga = df_fma(x, y, ga);
+        // NPL > 0: the lane's pieces of both columns of A and W in registers, loaded at once
+        df64 xa[NPL > 0 ? NPL : 1], ya[NPL > 0 ? NPL : 1], xw[NPL > 0 ? NPL : 1], yw[NPL > 0 ? NPL : 1];
+        if constexpr (NPL > 0) {
+#pragma unroll
+          for (int u = 0; u < NPL; ++u) {
+            const int i = lane + 32 * u;
+            xa[u] = i < r ? ap[i] : df_zero();
+            ya[u] = i < r ? aq[i] : df_zero();
+            xw[u] = i < c ? wp[i] : df_zero();
+            yw[u] = i < c ? wq[i] : df_zero();
+          }
+#pragma unroll
+          for (int u = 0; u < NPL; ++u) {
+            if (lane + 32 * u < r) {
+              al = df_fma(xa[u], xa[u], al);
+              be = df_fma(ya[u], ya[u], be);
+              ga = df_fma(xa[u], ya[u], ga);
+            }
+          }
+        } else {
+          for (int i = lane; i < r; i += 32) {
+            const df64 x = ap[i], y = aq[i];
+            al = df_fma(x, x, al);
+            be = df_fma(y, y, be);
+            ga = df_fma(x, y, ga);
+          }
         }
         al = warp_sum_df(al);
         be = warp_sum_df(be);
@@ -244,17 +268,30 @@ __global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
         }
         const df64 cs = df_div(make_df(1.f, 0.f), df_sqrt(df_add(make_df(1.f, 0.f), df_mul(t, t))));
         const df64 sn = df_mul(cs, t);
-        for (int i = lane; i < r; i += 32) {
-          const df64 x = ap[i], y = aq[i];
-          ap[i] = df_sub(df_mul(cs, x), df_mul(sn, y));
-          aq[i] = df_add(df_mul(sn, x), df_mul(cs, y));
-        }
-        df64* wp = colW(p);
-        df64* wq = colW(q);
-        for (int i = lane; i < c; i += 32) {
-          const df64 x = wp[i], y = wq[i];
-          wp[i] = df_sub(df_mul(cs, x), df_mul(sn, y));
-          wq[i] = df_add(df_mul(sn, x), df_mul(cs, y));
+        if constexpr (NPL > 0) {
+#pragma unroll
+          for (int u = 0; u < NPL; ++u) {
+            const int i = lane + 32 * u;
+            if (i < r) {
+              ap[i] = df_sub(df_mul(cs, xa[u]), df_mul(sn, ya[u]));
+              aq[i] = df_add(df_mul(sn, xa[u]), df_mul(cs, ya[u]));
+            }
+            if (i < c) {
+              wp[i] = df_sub(df_mul(cs, xw[u]), df_mul(sn, yw[u]));
+              wq[i] = df_add(df_mul(sn, xw[u]), df_mul(cs, yw[u]));
+            }
+          }
+        } else {
+          for (int i = lane; i < r; i += 32) {
+            const df64 x = ap[i], y = aq[i];
+            ap[i] = df_sub(df_mul(cs, x), df_mul(sn, y));
+            aq[i] = df_add(df_mul(sn, x), df_mul(cs, y));
+          }
+          for (int i = lane; i < c; i += 32) {
+            const df64 x = wp[i], y = wq[i];
+            wp[i] = df_sub(df_mul(cs, x), df_mul(sn, y));
+            wq[i] = df_add(df_mul(sn, x), df_mul(cs, y));
+          }
         }
         if (lane == 0) rotated_s = 1;
       }
@@ -327,6 +364,7 @@ __global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
 // shared memory (as k_small_svd_cluster), then the two Newton-Schulz steps
 // and A = B W with their entries split over the cluster's threads.  Same
 // arithmetic per entry as svd_precondition_body.
+template <int NPL>
 __global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
     k_svd_precondition_cluster(const df64* __restrict__ B, int ldb, int r, int c, df64* __restrict__ A,
                                df64* __restrict__ W, df64* __restrict__ T1, int cc, int max_sweeps, float tol32) {
@@ -363,12 +401,34 @@ __global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
         if (p >= c || q >= c) continue;
         float* ap = colA(p);
         float* aq = colA(q);
+        float* wp = colW(p);
+        float* wq = colW(q);
         float al = 0.f, be = 0.f, ga = 0.f;
-        for (int i = lane; i < r; i += 32) {
-          const float x = ap[i], y = aq[i];
-          al = fmaf(x, x, al);
-          be = fmaf(y, y, be);
-          ga = fmaf(x, y, ga);
+        float xa[NPL > 0 ? NPL : 1], ya[NPL > 0 ? NPL : 1], xw[NPL > 0 ? NPL : 1], yw[NPL > 0 ? NPL : 1];
+        if constexpr (NPL > 0) {
+#pragma unroll
+          for (int u = 0; u < NPL; ++u) {
+            const int i = lane + 32 * u;
+            xa[u] = i < r ? ap[i] : 0.f;
+            ya[u] = i < r ? aq[i] : 0.f;
+            xw[u] = i < c ? wp[i] : 0.f;
+            yw[u] = i < c ? wq[i] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < NPL; ++u) {
+            if (lane + 32 * u < r) {
+              al = fmaf(xa[u], xa[u], al);
+              be = fmaf(ya[u], ya[u], be);
+              ga = fmaf(xa[u], ya[u], ga);
+            }
+          }
+        } else {
+          for (int i = lane; i < r; i += 32) {
+            const float x = ap[i], y = aq[i];
+            al = fmaf(x, x, al);
+            be = fmaf(y, y, be);
+            ga = fmaf(x, y, ga);
+          }
         }
 #pragma unroll
         for (int m = 16; m; m >>= 1) {
@@ -382,17 +442,30 @@ __global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_CL_THREADS)
         const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
         const float cs = 1.f / sqrtf(1.f + t * t);
         const float sn = cs * t;
-        for (int i = lane; i < r; i += 32) {
-          const float x = ap[i], y = aq[i];
-          ap[i] = cs * x - sn * y;
-          aq[i] = sn * x + cs * y;
-        }
-        float* wp = colW(p);
-        float* wq = colW(q);
-        for (int i = lane; i < c; i += 32) {
-          const float x = wp[i], y = wq[i];
-          wp[i] = cs * x - sn * y;
-          wq[i] = sn * x + cs * y;
+        if constexpr (NPL > 0) {
+#pragma unroll
+          for (int u = 0; u < NPL; ++u) {
+            const int i = lane + 32 * u;
+            if (i < r) {
+              ap[i] = cs * xa[u] - sn * ya[u];
+              aq[i] = sn * xa[u] + cs * ya[u];
+            }
+            if (i < c) {
+              wp[i] = cs * xw[u] - sn * yw[u];
+              wq[i] = sn * xw[u] + cs * yw[u];
+            }
+          }
+        } else {
+          for (int i = lane; i < r; i += 32) {
+            const float x = ap[i], y = aq[i];
+            ap[i] = cs * x - sn * y;
+            aq[i] = sn * x + cs * y;
+          }
+          for (int i = lane; i < c; i += 32) {
+            const float x = wp[i], y = wq[i];
+            wp[i] = cs * x - sn * y;
+            wq[i] = sn * x + cs * y;
+          }
         }
         if (lane == 0) rotated_s = 1;
       }
@@ -475,33 +548,65 @@ __global__ void k_restart_B(df64* B, int ldb, int nrows_clear, const df64* __res
   (void)alpha_res_unused;
 }
 
-// out[:, m] = sum_{i<r} Q[:, i] P[i, m] for m < ncol (P col-major with leading dim ldp)
+// out[:, m] = sum_{i<r} Q[:, i] P[i, m] for m < ncol (P col-major with leading dim ldp).
+// A block owns RZ_COLS output columns (blockIdx.x, fastest, so the column
+// groups of the same rows run together and share the rows of Q in L2) and
+// walks row blocks of 512 (blockIdx.y, grid-stride); each thread keeps a
+// 2-row x RZ_COLS register tile of lazy double-float accumulators,
+// renormalised every 32 terms; P's slice sits in shared memory as [i][m].
+constexpr int RZ_COLS = 16;
 __global__ void __launch_bounds__(256) k_ritz(const df64* __restrict__ Q, int64_t ldq, int r,
                                               const df64* __restrict__ P, int ldp, int ncol,
                                               df64* __restrict__ out, int64_t ldo, int64_t dim) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  df64* Pt = reinterpret_cast<df64*>(smem_raw);  // [r][32]
-  const int m0 = blockIdx.y * 32;
-  for (int e = threadIdx.x; e < r * 32; e += blockDim.x) {
-    const int i = e >> 5, mm = e & 31;
-    Pt[e] = (m0 + mm < ncol) ? P[(int64_t)(m0 + mm) * ldp + i] : df_zero();
+  df64* Ps = reinterpret_cast<df64*>(smem_raw);  // [r][RZ_COLS]
+  const int m0 = blockIdx.x * RZ_COLS;
+  for (int e = threadIdx.x; e < r * RZ_COLS; e += blockDim.x) {
+    const int i = e / RZ_COLS, mm = e % RZ_COLS;
+    Ps[e] = (m0 + mm < ncol) ? P[(int64_t)(m0 + mm) * ldp + i] : df_zero();
   }
   __syncthreads();
-  const int64_t row = (int64_t)blockIdx.x * 64 + (threadIdx.x & 63);
-  const int cg = threadIdx.x >> 6;
-  df64 acc[8];
+  const int64_t nrb = (dim + 511) / 512;
+  for (int64_t rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
+    const int64_t row = rb * 512 + 2 * threadIdx.x;
+    dacc acc[2][RZ_COLS];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc[j] = df_zero();
-  if (row < dim) {
-    for (int i = 0; i < r; ++i) {
-      const df64 q = Q[(int64_t)i * ldq + row];
+    for (int m = 0; m < RZ_COLS; ++m) acc[0][m] = acc[1][m] = dacc_zero();
+    if (row < dim) {
+      const df64* qr = Q + row;
+      for (int i = 0; i < r; ++i) {
+        const float4 q = ld_pair(qr + (int64_t)i * ldq, 0, dim - row);
+        const df64 q0 = make_df(q.x, q.y), q1 = make_df(q.z, q.w);
+        const float4* pp = reinterpret_cast<const float4*>(Ps + i * RZ_COLS);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[j] = df_fma(q, Pt[i * 32 + cg + 4 * j], acc[j]);
-    }
+        for (int mm = 0; mm < RZ_COLS / 2; ++mm) {
+          const float4 pv = pp[mm];
+          const df64 p0 = make_df(pv.x, pv.y), p1 = make_df(pv.z, pv.w);
+          dacc_fma(acc[0][2 * mm], q0, p0);
+          dacc_fma(acc[1][2 * mm], q1, p0);
+          dacc_fma(acc[0][2 * mm + 1], q0, p1);
+          dacc_fma(acc[1][2 * mm + 1], q1, p1);
+        }
+        if ((i & 31) == 31) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int m = m0 + cg + 4 * j;
-      if (m < ncol) out[(int64_t)m * ldo + row] = acc[j];
+          for (int m = 0; m < RZ_COLS; ++m) {
+            dacc_norm(acc[0][m]);
+            dacc_norm(acc[1][m]);
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < RZ_COLS; ++m) {
+        if (m0 + m < ncol) {
+          const df64 v0 = dacc_val(acc[0][m]), v1 = dacc_val(acc[1][m]);
+          df64* o = out + (int64_t)(m0 + m) * ldo + row;
+          if (row + 1 < dim) {
+            *reinterpret_cast<float4*>(o) = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+          } else {
+            o[0] = v0;
+          }
+        }
+      }
     }
   }
 }
@@ -634,6 +739,19 @@ void launch_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stream, cu
   prof_end(s, K_MISC, 8.0 * dim, 0.0);
 }
 
+// shared-memory limits of the cluster kernels, once per process
+static std::once_flag g_svd_cluster_once;
+static void svd_cluster_setup() {
+  std::call_once(g_svd_cluster_once, [] {
+    cudaFuncSetAttribute(k_svd_precondition_cluster<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, PRE_SMEM_MAX);
+    cudaFuncSetAttribute(k_svd_precondition_cluster<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, PRE_SMEM_MAX);
+    cudaFuncSetAttribute(k_svd_precondition_cluster<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, PRE_SMEM_MAX);
+    cudaFuncSetAttribute(k_small_svd_cluster<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SVD_STAGE_MAX);
+    cudaFuncSetAttribute(k_small_svd_cluster<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SVD_STAGE_MAX);
+    cudaFuncSetAttribute(k_small_svd_cluster<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SVD_STAGE_MAX);
+  });
+}
+
 void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, double tol_conv,
                       df64* est, unsigned* status, cudaStream_t s) {
   const int cc = c + (c & 1);
@@ -641,15 +759,20 @@ void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, 
   int warm = 0;
   const int nloc_p = (c + SVD_CL - 1) / SVD_CL;
   const size_t pre_cl_sm = (size_t)nloc_p * (r + c) * sizeof(float);
+  // column pieces per lane held in registers by the cluster kernels (0: loops over shared memory)
+  const int npl = ((r > c ? r : c) + 31) / 32;
+  svd_cluster_setup();
   if (c >= 16 && pre_cl_sm <= (size_t)PRE_SMEM_MAX) {
-    static std::once_flag attr_c;
-    std::call_once(attr_c, [] {
-      cudaFuncSetAttribute(k_svd_precondition_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           PRE_SMEM_MAX);
-    });
     prof_begin(s);
-    k_svd_precondition_cluster<<<SVD_CL, SVD_CL_THREADS, pre_cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc,
-                                                                         PRE_SWEEPS, 2e-6f);
+    if (npl <= 4)
+      k_svd_precondition_cluster<4><<<SVD_CL, SVD_CL_THREADS, pre_cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc,
+                                                                              PRE_SWEEPS, 2e-6f);
+    else if (npl <= 8)
+      k_svd_precondition_cluster<8><<<SVD_CL, SVD_CL_THREADS, pre_cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc,
+                                                                              PRE_SWEEPS, 2e-6f);
+    else
+      k_svd_precondition_cluster<0><<<SVD_CL, SVD_CL_THREADS, pre_cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, sw.P, cc,
+                                                                              PRE_SWEEPS, 2e-6f);
     prof_end(s, K_SVD_PRE, 0.0, 0.0);
     warm = 1;
   } else if (c >= 16 && pre_sm <= (size_t)PRE_SMEM_MAX) {
@@ -667,14 +790,15 @@ void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, 
   const int nloc = (c + SVD_CL - 1) / SVD_CL;
   const size_t cl_sm = ((size_t)nloc * (r + c) + nloc) * sizeof(df64);
   if (cl_sm <= (size_t)SVD_STAGE_MAX) {
-    static std::once_flag attr3;
-    std::call_once(attr3, [] {
-      cudaFuncSetAttribute(k_small_svd_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, SVD_STAGE_MAX);
-    });
     prof_begin(s);
-    k_small_svd_cluster<<<SVD_CL, SVD_CL_THREADS, cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, cc, sw.sigma, sw.P, sw.Q,
-                                                               sw.resid, sw.sigma_d, k, tol_conv, sw.conv, est,
-                                                               status, sw.max_sweeps, sw.rot_tol, warm);
+#define SSA_SVD_CL(NPL)                                                                                        \
+  k_small_svd_cluster<NPL><<<SVD_CL, SVD_CL_THREADS, cl_sm, s>>>(B, ldb, r, c, sw.A, sw.W, cc, sw.sigma, sw.P,  \
+                                                                 sw.Q, sw.resid, sw.sigma_d, k, tol_conv, sw.conv, \
+                                                                 est, status, sw.max_sweeps, sw.rot_tol, warm)
+    if (npl <= 4) SSA_SVD_CL(4);
+    else if (npl <= 8) SSA_SVD_CL(8);
+    else SSA_SVD_CL(0);
+#undef SSA_SVD_CL
     prof_end(s, K_SMALL_SVD, 0.0, 0.0);
     return;
   }
@@ -700,12 +824,13 @@ void launch_restart_B(df64* B, int ldb, int nrows_clear, const SvdWork& sw, int 
 
 void launch_ritz(const df64* Q, int64_t ldq, int r, const df64* P, int ldp, int ncol, df64* out, int64_t ldo,
                  int64_t dim, cudaStream_t s) {
-  dim3 grid((unsigned)((dim + 63) / 64), (unsigned)((ncol + 31) / 32));
-  const size_t sm = (size_t)r * 32 * sizeof(df64);
+  const int64_t nrb = (dim + 511) / 512;
+  dim3 grid((unsigned)((ncol + RZ_COLS - 1) / RZ_COLS), (unsigned)(nrb < 65535 ? nrb : 65535));
+  const size_t sm = (size_t)r * RZ_COLS * sizeof(df64);
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(MAXCOL + 2) * 32 * 8);
+                         (int)(MAXCOL + 2) * RZ_COLS * 8);
   });
   prof_begin(s);
   k_ritz<<<grid, 256, sm, s>>>(Q, ldq, r, P, ldp, ncol, out, ldo, dim);
