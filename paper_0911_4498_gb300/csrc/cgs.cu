@@ -136,12 +136,14 @@ __global__ void __launch_bounds__(256, (CPW <= 13 ? 2 : 1))
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   df64* st0 = reinterpret_cast<df64*>(smem_raw);
   const int stage_elems = ncols * LR;
+  // this warp's columns: c = wp + 8m for m < mycols (warp-uniform; the unrolled column
+  // loops stop there instead of predicating the unused slots)
+  const int mycols = ncols > wp ? (ncols - wp + 7) >> 3 : 0;
   df64 hr[CPW];
   dacc acc[CPW];
 #pragma unroll
   for (int m = 0; m < CPW; ++m) {
-    const int c = wp + 8 * m;
-    hr[m] = (UPD && c < ncols) ? h[c] : df_zero();
+    hr[m] = (UPD && m < mycols) ? h[wp + 8 * m] : df_zero();
     acc[m] = dacc_zero();
   }
   dacc nacc = dacc_zero();
@@ -152,9 +154,10 @@ __global__ void __launch_bounds__(256, (CPW <= 13 ? 2 : 1))
     const int64_t r0 = (int64_t)tile * LR;
     const bool ok = r0 + 2 * lane < dim;
 #pragma unroll
-    for (int m = 0; m < CPW; ++m)
-      if (wp + 8 * m < ncols)
-        cp_async16(st + 8 * m * LR, ok ? (const void*)(qlane + m * qstep + r0) : (const void*)Q, ok);
+    for (int m = 0; m < CPW; ++m) {
+      if (m >= mycols) break;
+      cp_async16(st + 8 * m * LR, ok ? (const void*)(qlane + m * qstep + r0) : (const void*)Q, ok);
+    }
   };
   // rows of w: under UPD the first 64 threads hold one row each (plain loads: w is written
   // by this pass); otherwise every lane holds its two rows (read-only path)
@@ -199,11 +202,10 @@ __global__ void __launch_bounds__(256, (CPW <= 13 ? 2 : 1))
       dacc a0 = dacc_zero(), a1 = dacc_zero();
 #pragma unroll
       for (int m = 0; m < CPW; ++m) {
-        if (wp + 8 * m < ncols) {
-          const float4 v = *reinterpret_cast<const float4*>(sl + 8 * m * LR);
-          dacc_fma(a0, make_df(v.x, v.y), hr[m]);
-          dacc_fma(a1, make_df(v.z, v.w), hr[m]);
-        }
+        if (m >= mycols) break;
+        const float4 v = *reinterpret_cast<const float4*>(sl + 8 * m * LR);
+        dacc_fma(a0, make_df(v.x, v.y), hr[m]);
+        dacc_fma(a1, make_df(v.z, v.w), hr[m]);
       }
       const df64 s0 = dacc_val(a0), s1 = dacc_val(a1);
       df64(*rb)[LR] = red[NRED == 2 ? (it & 1) : 0];
@@ -230,15 +232,17 @@ __global__ void __launch_bounds__(256, (CPW <= 13 ? 2 : 1))
       }
 #pragma unroll
       for (int m = 0; m < CPW; ++m) {
-        if (wp + 8 * m < ncols) {
-          const float4 v = *reinterpret_cast<const float4*>(sl + 8 * m * LR);
-          dacc_fma(acc[m], make_df(v.x, v.y), x0);
-          dacc_fma(acc[m], make_df(v.z, v.w), x1);
-        }
+        if (m >= mycols) break;
+        const float4 v = *reinterpret_cast<const float4*>(sl + 8 * m * LR);
+        dacc_fma(acc[m], make_df(v.x, v.y), x0);
+        dacc_fma(acc[m], make_df(v.z, v.w), x1);
       }
       if ((it & 15) == 15) {
 #pragma unroll
-        for (int m = 0; m < CPW; ++m) dacc_norm(acc[m]);
+        for (int m = 0; m < CPW; ++m) {
+          if (m >= mycols) break;
+          dacc_norm(acc[m]);
+        }
       }
     }
     wr = wr_n;
@@ -250,11 +254,9 @@ __global__ void __launch_bounds__(256, (CPW <= 13 ? 2 : 1))
   if (PROJ) {
 #pragma unroll
     for (int m = 0; m < CPW; ++m) {
-      const int c = wp + 8 * m;
-      if (c < ncols) {  // warp-uniform
-        const df64 v = warp_sum_df(dacc_val(acc[m]));
-        if (lane == 0) part[(int64_t)blockIdx.x * ldp + c] = v;
-      }
+      if (m >= mycols) break;  // warp-uniform
+      const df64 v = warp_sum_df(dacc_val(acc[m]));
+      if (lane == 0) part[(int64_t)blockIdx.x * ldp + wp + 8 * m] = v;
     }
   }
   __syncthreads();

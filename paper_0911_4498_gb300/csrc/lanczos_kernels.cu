@@ -553,7 +553,8 @@ __global__ void k_restart_B(df64* B, int ldb, int nrows_clear, const df64* __res
 // groups of the same rows run together and share the rows of Q in L2) and
 // walks row blocks of 512 (blockIdx.y, grid-stride); each thread keeps a
 // 2-row x RZ_COLS register tile of lazy double-float accumulators,
-// renormalised every 32 terms; P's slice sits in shared memory as [i][m].
+// renormalised every 32 terms, and loads its next row pair of Q one
+// iteration ahead; P's slice sits in shared memory as [i][m].
 constexpr int RZ_COLS = 16;
 __global__ void __launch_bounds__(256) k_ritz(const df64* __restrict__ Q, int64_t ldq, int r,
                                               const df64* __restrict__ P, int ldp, int ncol,
@@ -574,8 +575,10 @@ __global__ void __launch_bounds__(256) k_ritz(const df64* __restrict__ Q, int64_
     for (int m = 0; m < RZ_COLS; ++m) acc[0][m] = acc[1][m] = dacc_zero();
     if (row < dim) {
       const df64* qr = Q + row;
+      float4 qn = ld_pair(qr, 0, dim - row);  // the next row pair, one iteration ahead
       for (int i = 0; i < r; ++i) {
-        const float4 q = ld_pair(qr + (int64_t)i * ldq, 0, dim - row);
+        const float4 q = qn;
+        if (i + 1 < r) qn = ld_pair(qr + (int64_t)(i + 1) * ldq, 0, dim - row);
         const df64 q0 = make_df(q.x, q.y), q1 = make_df(q.z, q.w);
         const float4* pp = reinterpret_cast<const float4*>(Ps + i * RZ_COLS);
 #pragma unroll
