@@ -70,8 +70,8 @@ WORKLOADS = {
 # unchanged (sha256 of its file), else the line reports traffic null.
 NCU_TRAFFIC = {
     "cgs_update_proj": {"ratio": 0.983, "file": "paper_0911_4498_gb300/csrc/cgs.cu",
-                        "sha256": "fe61a56080808ed7077b10c5fcfbfa7bcb62d5af5ec496da6d171195b5d47d79",
-                        "profile": "profiles/cgs_tiles_many_sines_N1M_dram.md"},
+                        "sha256": "adea783d09506c0ccc3e2356cd0236d643bde76ce6498bb033ef36ea017d53f3",
+                        "profile": "profiles/cgs_lanes_many_sines_N1M_dram.md"},
 }
 
 
