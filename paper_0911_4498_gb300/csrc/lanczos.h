@@ -25,7 +25,14 @@ struct ReorthWork {
   df64* h;       // projection coefficients of the first pass; h[ncols] = ||w||^2 (MAXCOL + 1)
   df64* h2;      // the same for the second pass; h2[ncols] = ||w'||^2 (MAXCOL + 1)
   int* gate;     // 1 when the third pass must run (Kahan-Parlett test on the device)
-  df64* nrm;     // squared norm after the last update
+  df64* nrm;     // squared norm after the last update (see nrm_blocks)
+  // launch_cgs2 may leave the final squared norm as per-block partial sums,
+  // column nrm_col of the first nrm_blocks rows of part2, for the following
+  // launch_normalize_coop to add up; nrm_blocks == 0, or *nrm_gate == 0 on the
+  // device, means *nrm holds it
+  int nrm_blocks;
+  int nrm_col;
+  const int* nrm_gate;
   int* counter;  // last-block counter (returns to 0 after each kernel)
   df64* coop;    // [coop_blocks()][MAXCOL + 1] scratch of the breakdown branch
   unsigned* status;  // device status word (SSA_DEV_* bits)
@@ -43,8 +50,9 @@ struct SvdWork {
 int reorth_blocks(int64_t dim);
 int fused_tiles(int64_t dim);
 void reorth_setup();
-// Classical Gram-Schmidt of w against the ncols columns of Q, then
-// nrm2 <- ||w||^2.  REORTH_ONCE: one projection and update (two passes over
+// Classical Gram-Schmidt of w against the ncols columns of Q, then the squared
+// norm ||w||^2 for the next launch_normalize_coop (in *rw.nrm, or as partial
+// sums that it adds up).  REORTH_ONCE: one projection and update (two passes over
 // Q).  REORTH_GATED: a second projection; its update (a third pass) runs only
 // when ||w'||^2 < ||w||^2 / 2 after the first (Kahan-Parlett), so the result
 // is orthogonal to Q to working precision either way.  Bases wider than

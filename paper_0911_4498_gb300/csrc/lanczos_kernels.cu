@@ -83,12 +83,29 @@ __global__ void __launch_bounds__(256) k_normalize_coop(df64* __restrict__ w, in
                                                         df64* __restrict__ bentry, df64* est,
                                                         const df64* __restrict__ Q, int64_t ldq, int ncols,
                                                         df64* __restrict__ scratch, int lds, uint64_t seed,
-                                                        uint64_t stream, unsigned* status) {
+                                                        uint64_t stream, unsigned* status,
+                                                        const df64* __restrict__ npart, int nblk, int ldnp,
+                                                        int ncol, const int* ngate) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   __shared__ df64 sh[32];
   __shared__ df64 hs[MAXCOL + 4];
-  const df64 beta = df_sqrt(*nrm2);
+  // ||w||^2: *nrm2, or the sum of the reorthogonalisation's per-block partials (npart[b][ncol],
+  // b < nblk; lane-strided then a warp butterfly, the same value in every block)
+  if (threadIdx.x < 32) {
+    df64 v;
+    if (nblk > 0 && !(ngate && *ngate == 0)) {
+      df64 a = df_zero();
+      for (int b = threadIdx.x; b < nblk; b += 32) a = df_add(a, npart[(int64_t)b * ldnp + ncol]);
+      v = warp_sum_df(a);
+    } else {
+      v = *nrm2;
+    }
+    if (threadIdx.x == 0) sh[0] = v;
+  }
+  __syncthreads();
+  const df64 beta = df_sqrt(sh[0]);
+  __syncthreads();  // sh is reused below
   if (!isfinite(beta.hi) && tid == 0) atomicOr(status, SSA_DEV_NONFINITE);
   const float thr = 1e-14f * est->hi;
   if (beta.hi > thr && beta.hi > 0.f && isfinite(beta.hi)) {
@@ -729,7 +746,11 @@ int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64
   int lds = MAXCOL + 1;
   const df64* nrm = rw.nrm;
   df64* scratch = rw.coop;
-  void* args[] = {&w, &dim, &nrm, &qcol, &bentry, &est, &Q, &ldq, &ncols, &scratch, &lds, &seed, &stream, &status};
+  const df64* npart = rw.part2;
+  int nblk = rw.nrm_blocks, ldnp = rw.ldp2, ncol = rw.nrm_col;
+  const int* ngate = rw.nrm_gate;
+  void* args[] = {&w,    &dim,  &nrm,    &qcol,   &bentry, &est,  &Q,    &ldq,  &ncols, &scratch,
+                  &lds,  &seed, &stream, &status, &npart,  &nblk, &ldnp, &ncol, &ngate};
   prof_begin(s);
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_normalize_coop, dim3(blocks), dim3(256), args, 0, s);
   prof_end(s, K_NORMALIZE, 16.0 * dim, 0.0);
