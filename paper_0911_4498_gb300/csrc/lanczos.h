@@ -60,8 +60,6 @@ void reorth_setup();
 enum { REORTH_ONCE = 1, REORTH_GATED = 2 };
 void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, int mode,
                  cudaStream_t s);
-void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est, int* flag, int mode,
-                      uint64_t seed, uint64_t stream, unsigned* status, cudaStream_t s);
 int coop_blocks();
 int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est,
                           const df64* Q, int64_t ldq, int ncols, uint64_t seed, uint64_t stream, unsigned* status,

@@ -17,60 +17,12 @@ __global__ void k_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stre
     w[i] = sm64_uniform_pm1(seed, stream, i);
 }
 
-// Normalise w into column qcol and record the coupling coefficient.
-//   mode 0: beta = sqrt(nrm2); if beta <= 1e-14 * est (breakdown, including
-//           beta == 0) the coefficient is recorded as 0, w is replaced by a
-//           seeded random vector and *flag = 1 so that the conditional
-//           reorthogonalisation that follows runs; otherwise *flag = 0.
-//   mode 1: only when *flag: normalise the reorthogonalised random vector;
-//           if it vanished (the basis already spans the space) store zeros.
-// est (largest coupling / singular value seen) is raised by block 0 at the
-// end; other blocks may read the old or the new value, which gives the same
-// decision because the new value is beta itself.
-__global__ void k_normalize(df64* __restrict__ w, int64_t dim, const df64* __restrict__ nrm2,
-                            df64* __restrict__ qcol, df64* __restrict__ bentry, df64* est, int* flag, int mode,
-                            uint64_t seed, uint64_t stream, unsigned* status) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if (mode == 1 && *flag == 0) return;
-  const df64 beta = df_sqrt(*nrm2);
-  if (!isfinite(beta.hi)) {
-    if (tid == 0) atomicOr(status, SSA_DEV_NONFINITE);
-  }
-  if (mode == 0) {
-    const float thr = 1e-14f * est->hi;
-    if (beta.hi > thr && beta.hi > 0.f && isfinite(beta.hi)) {
-      const df64 inv = df_div(make_df(1.f, 0.f), beta);
-      for (int64_t i = tid; i < dim; i += stride) qcol[i] = df_mul(w[i], inv);
-      __syncthreads();
-      if (tid == 0) {
-        *bentry = beta;
-        if (df_gt(beta, *est)) *est = beta;
-        *flag = 0;
-      }
-    } else {
-      for (int64_t i = tid; i < dim; i += stride) w[i] = sm64_uniform_pm1(seed, stream, i);
-      if (tid == 0) {
-        *bentry = df_zero();
-        *flag = 1;
-        atomicOr(status, SSA_DEV_BREAKDOWN);
-      }
-    }
-  } else {
-    // the random vector had norm ~ sqrt(dim/3) before orthogonalisation
-    const float ref = sqrtf((float)dim / 3.f);
-    const bool alive = beta.hi > 1e-6f * ref;
-    const df64 inv = alive ? df_div(make_df(1.f, 0.f), beta) : df_zero();
-    for (int64_t i = tid; i < dim; i += stride) qcol[i] = df_mul(w[i], inv);
-  }
-}
-
-__global__ void k_clear_flag(int* flag) { *flag = 0; }
-
 namespace cg = cooperative_groups;
 
 // Normalise w into qcol and record the coupling coefficient (one cooperative
-// launch).  Usual case: beta = sqrt(nrm2) > 1e-14 * est, qcol = w / beta.
+// launch).  ||w||^2 is *nrm2 or, when the reorthogonalisation left it as
+// per-block partial sums, their sum.  Usual case: beta = ||w|| > 1e-14 * est,
+// qcol = w / beta.
 // Breakdown (beta at or below that level, including 0): the coefficient is
 // recorded as 0 and w is replaced by a seeded random vector, orthogonalised
 // against the ncols basis columns by CGS2 inside the kernel (grid-wide
@@ -716,14 +668,6 @@ static int grid_for(int64_t n, int threads, int cap) {
   if (b < 1) b = 1;
   if (b > cap) b = cap;
   return (int)b;
-}
-
-void launch_normalize(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est, int* flag, int mode,
-                      uint64_t seed, uint64_t stream, unsigned* status, cudaStream_t s) {
-  prof_begin(s);
-  k_normalize<<<grid_for(dim, 256, 1184), 256, 0, s>>>(w, dim, rw.nrm, qcol, bentry, est, flag, mode, seed, stream,
-                                                       status);
-  prof_end(s, mode == 0 ? K_NORMALIZE : K_GATED, mode == 0 ? 16.0 * dim : 0.0, 0.0);
 }
 
 int coop_blocks() {
