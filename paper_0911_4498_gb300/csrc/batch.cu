@@ -30,9 +30,9 @@ constexpr int BT = 512;                 // threads per CTA
 constexpr int B_SMEM = 128 * 1024;      // dynamic shared memory (FFT buffer, reused by every phase)
 constexpr int B_MAXD = 72;              // largest Krylov dimension of a batched series
 constexpr int B_MAXC = B_MAXD + 2;      // basis columns / projected-matrix size
-constexpr int B_FR = 64;                // CGS tile rows
-constexpr int B_FRP = 66;               // CGS tile column stride
-constexpr int B_NST = 3;                // CGS pipeline stages: 3 x (73 x 66 + 64) df64 fit the 128 KB buffer
+constexpr int B_FR = 64;                // CGS tile rows (32 lanes x 2 rows)
+constexpr int B_NST = 3;                // CGS pipeline stages: 3 x 74 columns x 64 rows df64 (111 KB) and the
+                                        // row partials fit the 128 KB buffer
 
 struct BSeries {
   int64_t f_off, N, L, K;  // user sizes
@@ -241,114 +241,160 @@ SSA_D void cta_matvec(const Geom& g, int transpose, const df64* x, df64* y, cons
 }
 
 // ---------------------------------------------------------------- CGS2 in one CTA
-// One pass over the basis Q (dim x ncols) in tiles of B_FR rows, double
-// buffered in shared memory by 16-byte asynchronous copies:
+// One pass over the basis Q (dim x ncols) in tiles of B_FR = 64 rows:
 //   UPD:  w <- w - Q h_in;   PROJ: h_out[c] = Q[:, c] . w (c < ncols), h_out[ncols] = w.w
 //   !PROJ: *nrm_out = w.w
+// Warp wp owns the columns c = wp + 16m and lane l the rows 2l, 2l+1 of every
+// tile, so each lane stages (16-byte asynchronous copies, B_NST tiles deep)
+// and reads back only what it copied itself: the basis tiles need no
+// barrier.  Under UPD every warp forms the partial row sums of its columns;
+// after one barrier eight threads per row add the sixteen partials (pairs,
+// then a three-level butterfly: a fixed order) and the first of them writes
+// x = w - Q h_in (to shared memory when PROJ follows, and to w).  Under PROJ
+// each lane accumulates its columns' products with its two rows of x over all
+// tiles in registers; one warp reduction per column at the end.  Rows of w are
+// prefetched into registers one tile ahead.
+constexpr int B_W = BT / 32;                    // warps per CTA
+constexpr int B_CPW = (B_MAXC + B_W - 1) / B_W;  // basis columns per warp at most
 template <bool UPD, bool PROJ>
-SSA_D void cta_cgs_pass(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, const df64* h_in, df64* h_out,
-                        df64* nrm_out, df64* stbuf) {
-  const int tid = threadIdx.x;
-  const int stage_elems = ncols * B_FRP + B_FR;
+__device__ __noinline__ void cta_cgs_pass(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim,
+                                          const df64* h_in, df64* h_out, df64* nrm_out, df64* stbuf) {
+  constexpr int NRED = (UPD && !PROJ) ? 2 : 1;
+  static_assert(B_NST * B_MAXC * B_FR + 2 * B_W * B_FR + B_FR <= B_SMEM / 8, "CGS staging exceeds the buffer");
+  static_assert(B_W == 16 && BT / 8 == B_FR, "the row reduction pairs 16 warp partials over 8 threads per row");
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const int ntiles = (int)((dim + B_FR - 1) / B_FR);
-  auto issue = [&](int stg, int tile) {
+  const int stage_elems = ncols * B_FR;
+  df64* red0 = stbuf + B_NST * B_MAXC * B_FR;   // [NRED][B_W][B_FR] row partials
+  df64* xs = red0 + 2 * B_W * B_FR;             // [B_FR] updated rows
+  __shared__ df64 nred[B_W];
+  const int mycols = ncols > wp ? (ncols - wp + B_W - 1) / B_W : 0;  // warp-uniform
+  df64 hr[B_CPW];
+  dacc acc[B_CPW];
+  __syncthreads();  // the buffer's previous users are done
+#pragma unroll
+  for (int m = 0; m < B_CPW; ++m) {
+    hr[m] = (UPD && m < mycols) ? h_in[wp + B_W * m] : df_zero();
+    acc[m] = dacc_zero();
+  }
+  dacc nacc = dacc_zero();
+  const df64* qlane = Q + (int64_t)wp * ldq + 2 * lane;
+  const int64_t qstep = (int64_t)B_W * ldq;
+  auto issue = [&](int stg, int tile) {  // this lane's 16-byte pieces (column c at c * B_FR)
+    df64* st = stbuf + stg * stage_elems + wp * B_FR + 2 * lane;
     const int64_t r0 = (int64_t)tile * B_FR;
-    df64* st = stbuf + stg * stage_elems;
-    for (int e = tid; e < (ncols + 1) * (B_FR / 2); e += BT) {
-      const int c = e / (B_FR / 2), l = e - c * (B_FR / 2);
-      const int64_t row = r0 + 2 * l;
-      const bool ok = row < dim;
-      if (c < ncols)
-        cp_async16(st + c * B_FRP + 2 * l, ok ? (const void*)(Q + (int64_t)c * ldq + row) : (const void*)Q, ok);
-      else
-        cp_async16(st + ncols * B_FRP + 2 * l, ok ? (const void*)(w + row) : (const void*)w, ok);
+    const bool ok = r0 + 2 * lane < dim;
+#pragma unroll
+    for (int m = 0; m < B_CPW; ++m) {
+      if (m >= mycols) break;
+      cp_async16(st + B_W * m * B_FR, ok ? (const void*)(qlane + m * qstep + r0) : (const void*)Q, ok);
     }
   };
-  dacc acc = dacc_zero();
-  df64 nrm = df_zero();
-  // B_NST-stage pipeline: tiles tile+1 .. tile+B_NST-1 are in flight while tile is processed
+  const int rrow = tid >> 3, rq = tid & 7;  // UPD: eight threads per row
+  auto wrow = [&](int tile) -> df64 {
+    const int64_t row = (int64_t)tile * B_FR + rrow;
+    return row < dim ? w[row] : df_zero();
+  };
+  auto wpair = [&](int tile) -> float4 { return ld_pair(w, (int64_t)tile * B_FR + 2 * lane, dim); };
   for (int p = 0; p < B_NST - 1; ++p) {
     if (p < ntiles) issue(p, p);
     cp_async_commit();
   }
+  df64 wr = df_zero();
+  float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (ntiles > 0) {
+    if (UPD) {
+      if (rq == 0) wr = wrow(0);
+    } else {
+      wv = wpair(0);
+    }
+  }
   for (int tile = 0; tile < ntiles; ++tile) {
-    const int stage = tile % B_NST;
     const int ahead = tile + B_NST - 1;
     if (ahead < ntiles) issue(ahead % B_NST, ahead);
     cp_async_commit();
-    cp_async_wait<B_NST - 1>();
-    __syncthreads();
-    const df64* Qs = stbuf + stage * stage_elems;
-    df64* ws = const_cast<df64*>(Qs) + ncols * B_FRP;
-    const int64_t r0 = (int64_t)tile * B_FR;
-    {  // 32 row pairs x 16 threads per pair
-      const int rp = tid >> 4, q = tid & 15;
-      dacc a0 = dacc_zero(), a1 = dacc_zero();
+    df64 wr_n = wr;
+    float4 wv_n = wv;
+    if (tile + 1 < ntiles) {
       if (UPD) {
-        for (int c = q; c < ncols; c += 16) {
-          const float4 v = *reinterpret_cast<const float4*>(Qs + c * B_FRP + 2 * rp);
-          const df64 hc = h_in[c];
-          dacc_fma(a0, make_df(v.x, v.y), hc);
-          dacc_fma(a1, make_df(v.z, v.w), hc);
-        }
+        if (rq == 0) wr_n = wrow(tile + 1);
+      } else {
+        wv_n = wpair(tile + 1);
       }
-      df64 s0 = dacc_val(a0), s1 = dacc_val(a1);
+    }
+    cp_async_wait<B_NST - 1>();
+    const df64* sl = stbuf + (tile % B_NST) * stage_elems + wp * B_FR + 2 * lane;
+    const int64_t r0 = (int64_t)tile * B_FR;
+    if (UPD) {
+      dacc a0 = dacc_zero(), a1 = dacc_zero();
 #pragma unroll
-      for (int m = 1; m < 16; m <<= 1) {
-        s0 = df_add(s0, shfl_xor_df(s0, m));
-        s1 = df_add(s1, shfl_xor_df(s1, m));
+      for (int m = 0; m < B_CPW; ++m) {
+        if (m >= mycols) break;
+        const float4 v = *reinterpret_cast<const float4*>(sl + B_W * m * B_FR);
+        dacc_fma(a0, make_df(v.x, v.y), hr[m]);
+        dacc_fma(a1, make_df(v.z, v.w), hr[m]);
       }
+      const df64 s0 = dacc_val(a0), s1 = dacc_val(a1);
+      df64* rb = red0 + (NRED == 2 ? (tile & 1) : 0) * (B_W * B_FR);
+      *reinterpret_cast<float4*>(rb + wp * B_FR + 2 * lane) = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
       __syncthreads();
-      if (q == 0) {
-        const int64_t g0 = r0 + 2 * rp;
-        const df64 x0 = g0 < dim ? df_sub(ws[2 * rp], s0) : df_zero();
-        const df64 x1 = g0 + 1 < dim ? df_sub(ws[2 * rp + 1], s1) : df_zero();
-        ws[2 * rp] = x0;
-        ws[2 * rp + 1] = x1;
-        if (UPD) {
-          if (g0 < dim) w[g0] = x0;
-          if (g0 + 1 < dim) w[g0 + 1] = x1;
-        }
-        if (!PROJ) {
-          nrm = df_fma(x0, x0, nrm);
-          nrm = df_fma(x1, x1, nrm);
+      {
+        df64 sum = df_add(rb[(2 * rq) * B_FR + rrow], rb[(2 * rq + 1) * B_FR + rrow]);
+        sum = df_add(sum, shfl_xor_df(sum, 1));
+        sum = df_add(sum, shfl_xor_df(sum, 2));
+        sum = df_add(sum, shfl_xor_df(sum, 4));
+        if (rq == 0) {
+          const int64_t row = r0 + rrow;
+          const df64 x = row < dim ? df_sub(wr, sum) : df_zero();
+          if (PROJ) xs[rrow] = x;
+          if (row < dim) w[row] = x;
+          dacc_fma(nacc, x, x);
         }
       }
+      if (PROJ) __syncthreads();
     }
-    __syncthreads();
-    if (PROJ) {  // 4 threads per column (quarters of 16 rows); column ncols is w.w
-      const int c = tid >> 2, qt = tid & 3;
-      if (c <= ncols) {
-        const float4* col = reinterpret_cast<const float4*>((c < ncols ? Qs + c * B_FRP : ws) + qt * (B_FR / 4));
-        const float4* wv = reinterpret_cast<const float4*>(ws + qt * (B_FR / 4));
+    if (PROJ) {
+      const float4 xv = UPD ? *reinterpret_cast<const float4*>(xs + 2 * lane) : wv;
+      const df64 x0 = make_df(xv.x, xv.y), x1 = make_df(xv.z, xv.w);
+      if (!UPD && wp == 0) {
+        dacc_fma(nacc, x0, x0);
+        dacc_fma(nacc, x1, x1);
+      }
 #pragma unroll
-        for (int i = 0; i < B_FR / 8; ++i) {
-          const float4 qv = col[i], xv = wv[i];
-          dacc_fma(acc, make_df(qv.x, qv.y), make_df(xv.x, xv.y));
-          dacc_fma(acc, make_df(qv.z, qv.w), make_df(xv.z, xv.w));
+      for (int m = 0; m < B_CPW; ++m) {
+        if (m >= mycols) break;
+        const float4 v = *reinterpret_cast<const float4*>(sl + B_W * m * B_FR);
+        dacc_fma(acc[m], make_df(v.x, v.y), x0);
+        dacc_fma(acc[m], make_df(v.z, v.w), x1);
+      }
+      if ((tile & 15) == 15) {
+#pragma unroll
+        for (int m = 0; m < B_CPW; ++m) {
+          if (m >= mycols) break;
+          dacc_norm(acc[m]);
         }
-        dacc_norm(acc);
       }
     }
-    __syncthreads();
+    wr = wr_n;
+    wv = wv_n;
   }
   cp_async_wait<0>();
+  const df64 nv = warp_sum_df(dacc_val(nacc));
+  if (lane == 0) nred[wp] = nv;
   if (PROJ) {
-    df64 v = dacc_val(acc);
-    v = df_add(v, shfl_xor_df(v, 1));
-    v = df_add(v, shfl_xor_df(v, 2));
-    const int c = tid >> 2;
-    if ((tid & 3) == 0 && c <= ncols) h_out[c] = v;
-  } else {
-    __shared__ df64 red[BT / 32];
-    nrm = warp_sum_df(nrm);
-    if ((tid & 31) == 0) red[tid >> 5] = nrm;
-    __syncthreads();
-    if (tid == 0) {
-      df64 t = df_zero();
-      for (int i = 0; i < BT / 32; ++i) t = df_add(t, red[i]);
-      *nrm_out = t;
+#pragma unroll
+    for (int m = 0; m < B_CPW; ++m) {
+      if (m >= mycols) break;  // warp-uniform
+      const df64 v = warp_sum_df(dacc_val(acc[m]));
+      if (lane == 0) h_out[wp + B_W * m] = v;
     }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    df64 t = nred[0];
+    for (int q = 1; q < B_W; ++q) t = df_add(t, nred[q]);
+    if (PROJ) h_out[ncols] = t;
+    else *nrm_out = t;
   }
   __syncthreads();
 }
