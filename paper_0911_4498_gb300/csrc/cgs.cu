@@ -1,7 +1,8 @@
 // Reorthogonalisation against the Lanczos basis (section 3.2.2) by
-// classical Gram-Schmidt: the fused lane-owned passes over the basis, their
-// reductions with the Kahan-Parlett gate of the third pass, the wide-basis
-// fallback passes, and the launcher.  All vectors are double-float (df64).
+// classical Gram-Schmidt: the launcher of the fused lane-owned passes (the
+// kernel is in cgs_lanes.cuh), their reductions with the Kahan-Parlett gate
+// of the third pass, and the wide-basis fallback passes.  All vectors are
+// double-float (df64).
 #include <mutex>
 #include "lanczos.h"
 #include "lanczos_dev.cuh"
