@@ -54,6 +54,9 @@ WORKLOADS = {
     # Poisson arrivals at 2000 requests/s into the request server: N log-uniform in [1e3, 1e6], L = N//2,
     # k ~ U{2..64}, 40 GiB admission budget; each step is one arrival window of --window seconds
     "serving_2000rps": dict(kind="serving", rate=2000.0, seed=4),
+    # trajectory-matrix products X v (Algorithm 2) at the long-series size: the library's kernels in
+    # both precisions, with cuFFT (torch.fft) doing the same product beside them as a timed comparison
+    "matvec_N1M": dict(kind="products", N=1 << 20, L=1 << 19, gen="many_sines", seed=1),
     # section 6.4 timing setup: Q = N/2, B = T = N/4, L = B/2, I = {1, 2}; unit = whole H-matrices
     "hmatrix_N4000": dict(kind="hmatrix", N=4000, seed=0),
     # section 6.3: replicas of the rank-5 series + N(0, 5^2), L = N/2, rank-5 reconstruction each
@@ -544,6 +547,107 @@ def _timed(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps, sampler.stop()
 
 
+def fft_product(f, L, M, dtype, device="cpu"):
+    """X x (Algorithm 2) through a library FFT (torch.fft: cuFFT on a GPU), for timed comparison.
+
+    The circulant column c = (f_{N-L+1..N}, 0 x (M-N), f_{1..N-L}) is transformed once; returns a
+    function mapping x (K values, a tensor) to X x (L values).  Not part of the library's path.
+    """
+    import torch
+    N = f.size
+    K = N - L + 1
+    c = np.zeros(M)
+    c[:L] = f[N - L:]
+    c[L + (M - N):] = f[:N - L]
+    chat = torch.fft.rfft(torch.from_numpy(c).to(device=device, dtype=dtype))
+    wbuf = torch.zeros(M, dtype=dtype, device=device)
+
+    def prod(xx):
+        wbuf[:K].copy_(xx.flip(0))
+        return torch.fft.irfft(torch.fft.rfft(wbuf) * chat, n=M)[:L]
+
+    return prod
+
+
+def run_gpu_products(args, w):
+    """Products per second of X v at N = 2^20 through the C ABI (device buffers), beside cuFFT."""
+    import math as _m
+    import torch
+    from paper_0911_4498_gb300 import build
+    build.build()
+    import paper_0911_4498_gb300 as ssa
+    N, L = w["N"], w["L"]
+    K = N - L + 1
+    f = series(w)
+    stream = torch.cuda.current_stream()
+    R = 20          # products per step
+    NV = 40         # input/output vectors the products rotate through (2 x 168 MB > L2)
+    rng = np.random.default_rng(7)
+    xs = torch.from_numpy(rng.standard_normal((NV, K))).cuda()
+    ys = torch.empty((NV, L), dtype=torch.float64, device="cuda")
+    rows = np.linspace(0, L - 1, 8).astype(np.int64)
+    xh = xs[0].cpu().numpy()
+    exact = np.array([_m.fsum(f[i:i + K] * xh) for i in rows])
+    scale = float(np.linalg.norm(f) * np.linalg.norm(xh))
+    res, M = {}, None
+    for name, prec in (("ssa_f64", ssa.SSA_PREC_F64), ("ssa_f32c", ssa.SSA_PREC_F32C)):
+        plan = ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=prec, stream=stream.cuda_stream))
+        ssa.ssa_set_series(plan, f)
+        M, _ = ssa.ssa_plan_info(plan)
+        cnt = [0]
+
+        def step():
+            for _ in range(R):
+                i = cnt[0] % NV
+                ssa.ssa_matvec(plan, 0, xs[i], ys[i], 1)
+                cnt[0] += 1
+
+        ms, clocks = _timed(step, args.steps, args.warmup)
+        ssa.ssa_matvec(plan, 0, xs[0], ys[0], 1)
+        torch.cuda.synchronize()
+        err = float(np.max(np.abs(ys[0].cpu().numpy()[rows] - exact)) / scale)
+        res[name] = {"ms_per_product": ms / R, "products_per_s": 1000.0 * R / ms, "max_err_normwise": err,
+                     "clocks": clocks}
+        ssa.ssa_plan_destroy(plan)
+    for name, dt in (("cufft_f64", torch.float64), ("cufft_f32", torch.float32)):
+        prod = fft_product(f, L, M, dt, "cuda")
+        xin = xs.to(dt)
+        outs = [None] * NV
+        cnt = [0]
+
+        def step():
+            for _ in range(R):
+                i = cnt[0] % NV
+                outs[i] = prod(xin[i])
+                cnt[0] += 1
+
+        ms, clocks = _timed(step, args.steps, args.warmup)
+        y0 = prod(xin[0]).double().cpu().numpy()
+        err = float(np.max(np.abs(y0[rows] - exact)) / scale)
+        res[name] = {"ms_per_product": ms / R, "products_per_s": 1000.0 * R / ms, "max_err_normwise": err,
+                     "clocks": clocks}
+    # algorithmic bytes of one product (input, output and the half spectrum, 8-byte values)
+    mv_bytes = 8.0 * (K + L) + 16.0 * (M // 2 + 1)
+    hbm, peak_kind = peaks()
+    ours = res["ssa_f64"]
+    achieved = mv_bytes / (ours["ms_per_product"] / 1000.0) / 1e9
+    line = {"metric": METRIC, "value": ours["products_per_s"], "unit": "products/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ours["ms_per_product"] * R,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "L": L, "K": K, "M": M, "products_per_step": R,
+                       "l2": "inputs and outputs rotate through 40 vectors each (2 x 168 MB), larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "X v (three four-step kernels)", "bytes_per_launch": mv_bytes,
+                         "peak_source": peak_kind},
+            "products": {k2: {kk: v for kk, v in r.items() if kk != "clocks"} for k2, r in res.items()},
+            "accuracy_reference": "8 sampled rows of X x summed exactly (math.fsum) on the host",
+            "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+            "clocks": ours["clocks"]}
+    print(json.dumps(line))
+    return 0
+
+
 def _oracle_rows(a):
     f, L, B, T, rows = a
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
@@ -785,6 +889,8 @@ def run_gpu(args):
         return run_gpu_bootstrap(args, w)
     if w.get("kind") == "precision":
         return run_gpu_precision(args, w)
+    if w.get("kind") == "products":
+        return run_gpu_products(args, w)
     N, L, k = w["N"], w["L"], w["k"]
     K = N - L + 1
     prec = ssa.SSA_PREC_F32C if args.precision == "f32c" else ssa.SSA_PREC_F64

@@ -48,3 +48,27 @@ def test_two_rank_aggregation_gloo():
 def test_single_rank_aggregation():
     import bench
     assert bench.aggregate(2.0, 4) == (2.0, 2.0, 4)
+
+
+def test_cufft_comparison_product_matches_explicit_X():
+    """The library-FFT comparison product bench.py times beside the kernels computes X x
+    (checked on CPU tensors against the explicit trajectory matrix, for several M >= N)."""
+    import numpy as np
+    import torch
+
+    import bench
+    from oracle import trajectory
+    rng = np.random.default_rng(3)
+    for N, L in [(17, 5), (100, 63), (1000, 500), (1025, 1000)]:
+        f = rng.standard_normal(N)
+        K = N - L + 1
+        X = trajectory.trajectory_matrix(f, L)
+        x = rng.standard_normal(K)
+        M0 = 1 << (N - 1).bit_length()
+        for M in (M0, 2 * M0):
+            for dt, tol in ((torch.float64, 1e-13), (torch.float32, 2e-6)):
+                prod = bench.fft_product(f, L, M, dt)
+                y = prod(torch.from_numpy(x).to(dt)).double().numpy()
+                scale = np.linalg.norm(f) * np.linalg.norm(x)
+                assert y.shape == (L,)
+                assert np.max(np.abs(y - X @ x)) <= tol * scale, (N, L, M, dt)
