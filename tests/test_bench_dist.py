@@ -1,5 +1,6 @@
-"""Host logic of the multi-GPU (replica) path of bench.py on CPU: two gloo ranks
-aggregate their timed regions into whole-job throughput = summed units / max time."""
+"""Host logic of bench.py on CPU: two gloo ranks aggregate their timed regions into
+whole-job throughput (summed units / max time); the cuFFT comparison product; the
+nvidia-smi clock and throttle-reason sampling."""
 import os
 import socket
 
@@ -72,3 +73,39 @@ def test_cufft_comparison_product_matches_explicit_X():
                 scale = np.linalg.norm(f) * np.linalg.norm(x)
                 assert y.shape == (L,)
                 assert np.max(np.abs(y - X @ x)) <= tol * scale, (N, L, M, dt)
+
+
+def _fake_smi(tmp_path, rows):
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n" + "".join(f"echo '{r}'\n" for r in rows))
+    fake.chmod(0o755)
+    return str(tmp_path)
+
+
+def test_clock_sampler_reads_clocks_and_reasons(tmp_path, monkeypatch):
+    """The throttle reasons that decide whether a bench run counts, parsed from nvidia-smi's CSV."""
+    import bench
+    rows = ["0, 2070, 2070, 900.50, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 1965, 2070, 1390.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 800.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"]
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, rows) + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    out = s.stop()
+    assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    rows = ["0, 1200, 2070, 1000.00, 0x0000000000000008, Active, Not Active, Active, Not Active"]
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, rows) + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    out = s.stop()
+    assert out["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and out["sm_mhz"] == 1200.0
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    import bench
+    monkeypatch.setenv("PATH", str(tmp_path))
+    s = bench.ClockSampler(0)
+    s.start()
+    out = s.stop()
+    assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
