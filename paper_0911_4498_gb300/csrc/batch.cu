@@ -254,6 +254,17 @@ SSA_D void cta_matvec(const Geom& g, int transpose, const df64* x, df64* y, cons
 // each lane accumulates its columns' products with its two rows of x over all
 // tiles in registers; one warp reduction per column at the end.  Rows of w are
 // prefetched into registers one tile ahead.
+// Two consecutive rows (row even, 16-byte aligned) of a vector this persistent kernel also writes,
+// read through L2 (coherent with the kernel's own earlier stores, unlike the read-only path);
+// rows >= dim read as 0.
+SSA_D float4 ld_pair_l2(const df64* p, int64_t row, int64_t dim) {
+  if (row + 1 < dim) return __ldcg(reinterpret_cast<const float4*>(p + row));
+  if (row < dim) {
+    const float2 a = __ldcg(reinterpret_cast<const float2*>(p + row));
+    return make_float4(a.x, a.y, 0.f, 0.f);
+  }
+  return make_float4(0.f, 0.f, 0.f, 0.f);
+}
 constexpr int B_W = BT / 32;                    // warps per CTA
 constexpr int B_CPW = (B_MAXC + B_W - 1) / B_W;  // basis columns per warp at most
 template <bool UPD, bool PROJ>
@@ -295,7 +306,7 @@ __device__ __noinline__ void cta_cgs_pass(const df64* Q, int64_t ldq, int ncols,
     const int64_t row = (int64_t)tile * B_FR + rrow;
     return row < dim ? w[row] : df_zero();
   };
-  auto wpair = [&](int tile) -> float4 { return ld_pair(w, (int64_t)tile * B_FR + 2 * lane, dim); };
+  auto wpair = [&](int tile) -> float4 { return ld_pair_l2(w, (int64_t)tile * B_FR + 2 * lane, dim); };
   for (int p = 0; p < B_NST - 1; ++p) {
     if (p < ntiles) issue(p, p);
     cp_async_commit();
