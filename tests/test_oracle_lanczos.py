@@ -12,7 +12,8 @@ def _match(a, b, k, tol_sigma):
     np.testing.assert_allclose(a["sigma"][:k], b["sigma"][:k], rtol=tol_sigma, atol=tol_sigma * s1)
 
 
-@pytest.mark.parametrize("N,L,k,seed", [(500, 250, 8, 0), (1000, 500, 10, 0), (777, 300, 12, 4), (1200, 900, 6, 2)])
+@pytest.mark.parametrize("N,L,k,seed", [(500, 250, 8, 0), (1000, 500, 10, 0), (777, 300, 12, 4), (1200, 900, 6, 2),
+                                        (4000, 500, 10, 3)])
 def test_lanczos_matches_jacobi(N, L, k, seed):
     f = synth.three_sines(N, seed=seed)
     a = ssa.decompose(f, L, k, method="jacobi")
