@@ -25,6 +25,19 @@ from .dft import fft_radix2, ifft_radix2
 from .trajectory import antidiagonal_counts
 
 
+def _ffts(fft: str):
+    """(forward, inverse) complex FFTs with the definitions of section 4.1 (inverse with 1/M).
+
+    "radix2" is the oracle's own FFT; "library" is numpy's, for sizes where the
+    pure-Python butterfly stages are too slow (pinned to "radix2" by a test).
+    """
+    if fft == "radix2":
+        return fft_radix2, ifft_radix2
+    if fft == "library":
+        return np.fft.fft, np.fft.ifft
+    raise ValueError(f"unknown fft {fft!r}")
+
+
 def fft_length(N: int) -> int:
     """Oracle FFT length: the next power of two >= 2N."""
     M = 1
@@ -45,28 +58,31 @@ def circulant_column(f: np.ndarray, L: int, M: int) -> np.ndarray:
     return c
 
 
-def spectrum(f: np.ndarray, L: int, M: int) -> np.ndarray:
+def spectrum(f: np.ndarray, L: int, M: int, fft: str = "radix2") -> np.ndarray:
     """c-hat = FFT_M(c) (Algorithm 2 step 2), computed once per (f, L)."""
-    return fft_radix2(circulant_column(f, L, M))
+    fwd, _ = _ffts(fft)
+    return fwd(circulant_column(f, L, M))
 
 
-def hankel_matvec(chat: np.ndarray, N: int, L: int, v: np.ndarray) -> np.ndarray:
+def hankel_matvec(chat: np.ndarray, N: int, L: int, v: np.ndarray, fft: str = "radix2") -> np.ndarray:
     """Algorithm 2: p = X v for v of length K."""
+    fwd, inv = _ffts(fft)
     M = chat.size
     K = N - L + 1
     w = np.zeros(M)
     w[:K] = np.asarray(v, dtype=np.float64)[::-1]     # (v_K, ..., v_1, 0, ..., 0)
-    p = ifft_radix2(fft_radix2(w) * chat)
+    p = inv(fwd(w) * chat)
     return p[:L].real                                  # p'_1..p'_L
 
 
-def hankel_rmatvec(chat: np.ndarray, N: int, L: int, u: np.ndarray) -> np.ndarray:
+def hankel_rmatvec(chat: np.ndarray, N: int, L: int, u: np.ndarray, fft: str = "radix2") -> np.ndarray:
     """Algorithm 3: p = X^T u for u of length L."""
+    fwd, inv = _ffts(fft)
     M = chat.size
     K = N - L + 1
     w = np.zeros(M)
     w[M - L:] = np.asarray(u, dtype=np.float64)[::-1]  # (0, ..., 0, u_L, ..., u_1)
-    p = ifft_radix2(fft_radix2(w) * chat)
+    p = inv(fwd(w) * chat)
     return p[M - K:].real                              # p'_L..p'_N when M = N
 
 

@@ -4,7 +4,9 @@ Oracle -- test infrastructure only.
 
 decompose(f, L, k):  leading k singular triples of the L-trajectory matrix
     (sections 2.1-2.2).  method="jacobi" forms X and runs one-sided Jacobi
-    (small N); method="lanczos" runs the oracle's GKL on Algorithms 2/3.
+    (small N); method="lanczos" runs the oracle's GKL on Algorithms 2/3, whose
+    FFTs are the oracle's own radix-2 (fft="radix2") or numpy's (fft="library",
+    for the largest sizes; the two are pinned to each other by a test).
     If L > K the K-trajectory matrix (= X^T) is decomposed and U, V swapped
     (the paper assumes L <= K without loss of generality).
     Sign rule (the SVD fixes each pair (u_i, v_i) only up to a common sign):
@@ -44,13 +46,14 @@ def sign_rule(U: np.ndarray, V: np.ndarray):
 
 
 def decompose(f, L: int, k: int, method: str = "auto", tol: float = 1e-14, seed: int = 0,
-              max_restarts: int = 200, d: int | None = None, max_steps: int | None = None):
+              max_restarts: int = 200, d: int | None = None, max_steps: int | None = None,
+              fft: str = "radix2"):
     f = np.asarray(f, dtype=np.float64)
     N = f.size
     validate(N, L, k)
     K = N - L + 1
     if L > K:
-        out = decompose(f, K, k, method, tol, seed, max_restarts, d, max_steps)
+        out = decompose(f, K, k, method, tol, seed, max_restarts, d, max_steps, fft)
         U, V = sign_rule(out["V"], out["U"])
         out.update(U=U, V=V)
         return out
@@ -64,9 +67,9 @@ def decompose(f, L: int, k: int, method: str = "auto", tol: float = 1e-14, seed:
     if method != "lanczos":
         raise ValueError(method)
     M = fast_hankel.fft_length(N)
-    chat = fast_hankel.spectrum(f, L, M)
-    res = lanczos.gkl_svd(lambda v: fast_hankel.hankel_matvec(chat, N, L, v),
-                          lambda u: fast_hankel.hankel_rmatvec(chat, N, L, u),
+    chat = fast_hankel.spectrum(f, L, M, fft)
+    res = lanczos.gkl_svd(lambda v: fast_hankel.hankel_matvec(chat, N, L, v, fft),
+                          lambda u: fast_hankel.hankel_rmatvec(chat, N, L, u, fft),
                           L, K, k, d=d, tol=tol, max_restarts=max_restarts, seed=seed,
                           max_steps=max_steps)
     U, V = sign_rule(res.U, res.V)

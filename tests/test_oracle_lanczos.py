@@ -84,3 +84,24 @@ def test_window_larger_than_K():
     b = ssa.decompose(f, 450, 6, method="jacobi")
     _match(a, b, 6, 1e-12)
     assert a["U"].shape == (450, 6) and a["V"].shape == (151, 6)
+
+
+def test_library_fft_option_matches_own_fft():
+    """The oracle's library-FFT option (used only where its own radix-2 FFT is too slow) gives the
+    same products and the same decomposition as its own FFT."""
+    f = synth.many_sines(5000, seed=2)
+    L, K = 2500, 2501
+    M = fast_hankel.fft_length(5000)
+    rng = np.random.default_rng(1)
+    v, u = rng.standard_normal(K), rng.standard_normal(L)
+    c_own, c_lib = fast_hankel.spectrum(f, L, M), fast_hankel.spectrum(f, L, M, "library")
+    scale_v, scale_u = np.linalg.norm(f) * np.linalg.norm(v), np.linalg.norm(f) * np.linalg.norm(u)
+    assert np.max(np.abs(fast_hankel.hankel_matvec(c_own, 5000, L, v)
+                         - fast_hankel.hankel_matvec(c_lib, 5000, L, v, "library"))) <= 1e-13 * scale_v
+    assert np.max(np.abs(fast_hankel.hankel_rmatvec(c_own, 5000, L, u)
+                         - fast_hankel.hankel_rmatvec(c_lib, 5000, L, u, "library"))) <= 1e-13 * scale_u
+    a = ssa.decompose(f, L, 10, method="lanczos", seed=0)
+    b = ssa.decompose(f, L, 10, method="lanczos", seed=0, fft="library")
+    _match(a, b, 10, 1e-12)
+    with pytest.raises(ValueError):
+        fast_hankel.spectrum(f, L, M, "other")
