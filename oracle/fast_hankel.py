@@ -86,8 +86,10 @@ def hankel_rmatvec(chat: np.ndarray, N: int, L: int, u: np.ndarray, fft: str = "
     return p[M - K:].real                              # p'_L..p'_N when M = N
 
 
-def rank1_hankelization(sigma: float, u: np.ndarray, v: np.ndarray, M: int | None = None) -> np.ndarray:
+def rank1_hankelization(sigma: float, u: np.ndarray, v: np.ndarray, M: int | None = None,
+                        fft: str = "radix2") -> np.ndarray:
     """Algorithm 4: diagonal average of sigma u v^T via a linear convolution."""
+    fwd, inv = _ffts(fft)
     u = np.asarray(u, dtype=np.float64)
     v = np.asarray(v, dtype=np.float64)
     L, K = u.size, v.size
@@ -100,5 +102,5 @@ def rank1_hankelization(sigma: float, u: np.ndarray, v: np.ndarray, M: int | Non
     up[:L] = u
     vp = np.zeros(M)
     vp[:K] = v
-    g = ifft_radix2(fft_radix2(vp) * fft_radix2(up)).real[:N]
+    g = inv(fwd(vp) * fwd(up)).real[:N]
     return sigma * g / antidiagonal_counts(N, L)

@@ -15,7 +15,8 @@ decompose(f, L, k):  leading k singular triples of the L-trajectory matrix
 reconstruct(N, L, sigma, U, V, groups):  for each index group I, the
     diagonal average of X_I = sum_{i in I} sigma_i u_i v_i^T (sections 2.3-2.4):
     method="naive" forms X_I and applies the three-case formula,
-    method="fft" sums Algorithm 4 over the group.
+    method="fft" sums Algorithm 4 over the group, on the oracle's own FFT or,
+    with fft="library", on numpy's (the full-size checks; pinned to "radix2").
 """
 from __future__ import annotations
 
@@ -78,7 +79,7 @@ def decompose(f, L: int, k: int, method: str = "auto", tol: float = 1e-14, seed:
             "steps": res.steps, "d": res.d}
 
 
-def reconstruct(N: int, L: int, sigma, U, V, groups, method: str = "naive") -> np.ndarray:
+def reconstruct(N: int, L: int, sigma, U, V, groups, method: str = "naive", fft: str = "radix2") -> np.ndarray:
     sigma = np.asarray(sigma, dtype=np.float64)
     out = np.zeros((len(groups), N))
     for g, idx in enumerate(groups):
@@ -88,7 +89,7 @@ def reconstruct(N: int, L: int, sigma, U, V, groups, method: str = "naive") -> n
             out[g] = trajectory.diagonal_average(Y)
         elif method == "fft":
             for i in idx:
-                out[g] += fast_hankel.rank1_hankelization(sigma[i], U[:, i], V[:, i])
+                out[g] += fast_hankel.rank1_hankelization(sigma[i], U[:, i], V[:, i], fft=fft)
         else:
             raise ValueError(method)
     return out

@@ -105,3 +105,21 @@ def test_library_fft_option_matches_own_fft():
     _match(a, b, 10, 1e-12)
     with pytest.raises(ValueError):
         fast_hankel.spectrum(f, L, M, "other")
+
+
+def test_library_fft_hankelization_matches_own_fft_and_naive():
+    """Algorithm 4 on numpy's FFT (the full-size reconstruction checks use it) equals the oracle's
+    own radix-2 FFT and the naive antidiagonal mean of section 2.4, for L <= K and L > K."""
+    from oracle import trajectory
+    rng = np.random.default_rng(5)
+    for N, L in ((300, 120), (301, 200), (4097, 2048)):
+        K = N - L + 1
+        u, v = rng.standard_normal(L), rng.standard_normal(K)
+        own = fast_hankel.rank1_hankelization(1.7, u, v)
+        lib = fast_hankel.rank1_hankelization(1.7, u, v, fft="library")
+        assert np.max(np.abs(own - lib)) <= 1e-13 * np.max(np.abs(own))
+        if N <= 400:
+            naive = trajectory.diagonal_average(1.7 * np.outer(u, v))
+            assert np.max(np.abs(lib - naive)) <= 1e-13 * np.max(np.abs(naive))
+    with pytest.raises(ValueError):
+        fast_hankel.rank1_hankelization(1.0, u, v, fft="other")
