@@ -111,24 +111,52 @@ def clusters(sigma, rel_gap=1e-6):
 
 
 def subspace_sin(A, B):
+    """Sine of the largest principal angle between span(A) and span(B), as the
+    2-norm of the part of B's orthonormal basis outside span(A) (accurate for
+    tiny angles, where 1 - cos^2 cancels)."""
     qa, _ = np.linalg.qr(A)
     qb, _ = np.linalg.qr(B)
-    s = np.linalg.svd(qa.T @ qb, compute_uv=False)
-    return math.sqrt(max(0.0, 1.0 - float(np.min(s)) ** 2))
+    r = qb - qa @ (qa.T @ qb)
+    return float(np.linalg.norm(r, 2))
 
 
-def compare_vectors(Ug, Uo, sigma, tol, rel_gap=1e-6, skip_below=None):
-    """Max vector error: |1 - |u_g.u_o|| for isolated triples, principal-angle
-    sine for clusters.  Triples with sigma below skip_below are not compared."""
+def vec_sin(a, b):
+    """Sine of the angle between the lines spanned by a and b (linear in the
+    angle, unlike 1 - |a.b|, which is about theta^2 / 2)."""
+    a = a / np.linalg.norm(a)
+    b = b / np.linalg.norm(b)
+    s = np.sign(float(a @ b)) or 1.0
+    # |a - s b| = 2 sin(theta / 2) is accurate for tiny angles; sin = that * cos(theta / 2)
+    h = float(np.linalg.norm(a - s * b))
+    return h * math.sqrt(max(0.0, 1.0 - h * h / 4.0))
+
+
+def compare_vectors(Ug, Uo, sigma, tol, rel_gap=1e-6, skip_below=None, res_tol=None, sigma_next=None):
+    """Max vector error: the sine of the angle between u_g and u_o for isolated
+    triples, the largest principal-angle sine for clusters.  Triples with sigma
+    below skip_below are not compared.
+
+    res_tol: a triple whose Ritz residual is at most res_tol * sigma_1 can be
+    off by sin(theta) <= res_tol * sigma_1 / gap (Wedin's sin-theta bound, gap
+    to the nearest other singular value, sigma_next being the first one not
+    returned); each triple or cluster is then allowed max(tol, that bound)."""
     worst = 0.0
+    sig = np.asarray(sigma, dtype=np.float64)
+    ext = np.append(sig, sigma_next) if sigma_next is not None else sig
     for cl in clusters(sigma, rel_gap):
         if skip_below is not None and sigma[cl[0]] < skip_below:
             continue
         if len(cl) == 1:
             i = cl[0]
-            e = abs(1.0 - abs(float(Ug[:, i] @ Uo[:, i])))
+            e = vec_sin(Ug[:, i], Uo[:, i])
         else:
             e = subspace_sin(Ug[:, cl], Uo[:, cl])
-        worst = max(worst, e)
-    assert worst <= tol, f"vector error {worst:.3e} > {tol:.1e}"
+        allowed = tol
+        if res_tol is not None:
+            others = np.delete(ext, cl)
+            if others.size:
+                gap = max(float(np.min(np.abs(others[:, None] - sig[cl][None, :]))), 1e-300)
+                allowed = max(tol, res_tol * float(sig[0]) / gap)
+        assert e <= allowed, f"vector error {e:.3e} > {allowed:.1e} (triples {cl})"
+        worst = max(worst, e / allowed * tol)
     return worst
