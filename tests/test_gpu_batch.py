@@ -71,7 +71,11 @@ def test_each_result_same_alone_and_in_the_mix(precision, tol):
             ssa.ssa_batch_destroy(b)
         rel = np.max(np.abs(sig - mix[j]["sigma"]) / mix[j]["sigma"])
         assert rel <= tol, (specs[j], rel)
-        compare_vectors(U.T.copy(), mix[j]["U"], sig, 1e-5 if precision == ssa.SSA_PREC_F32C else 1e-7)
+        # FP32 products: Ritz residuals up to ~1e-6 sigma_1 (Wedin bound); df64: rounding only
+        if precision == ssa.SSA_PREC_F32C:
+            compare_vectors(U.T.copy(), mix[j]["U"], sig, 1e-5, res_tol=1e-6)
+        else:
+            compare_vectors(U.T.copy(), mix[j]["U"], sig, 1e-7)
 
 
 def test_batch_agrees_with_plan_path():

@@ -58,7 +58,8 @@ def test_mixed_stream_matches_oracle():
         ref = ossa.decompose(_series(i, N), L, k, method="jacobi" if N <= 1500 else "lanczos")
         rel = np.max(np.abs(o["sigma"] - ref["sigma"]) / ref["sigma"])
         assert rel <= SIG_F32C, (N, L, k, rel)
-        compare_vectors(o["U"], ref["U"], ref["sigma"], 1e-4, skip_below=1e-2 * ref["sigma"][0])
+        # FP32 products: residuals up to ~1e-6 sigma_1, vectors within Wedin's bound
+        compare_vectors(o["U"], ref["U"], ref["sigma"], 1e-4, skip_below=1e-2 * ref["sigma"][0], res_tol=1e-6)
 
 
 def test_each_result_same_alone_and_in_the_mix():
@@ -79,7 +80,7 @@ def test_each_result_same_alone_and_in_the_mix():
         assert info["batched"] == mix[j]["info"]["batched"]
         rel = np.max(np.abs(sig - mix[j]["sigma"]) / mix[j]["sigma"])
         assert rel <= 1e-6, (MIX[j], rel)
-        compare_vectors(U.T.copy(), mix[j]["U"], sig, 1e-5, skip_below=1e-2 * sig[0])
+        compare_vectors(U.T.copy(), mix[j]["U"], sig, 1e-5, skip_below=1e-2 * sig[0], res_tol=1e-6)
 
 
 def test_f64_server_matches_plan_path():
