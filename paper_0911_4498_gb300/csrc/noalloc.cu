@@ -22,6 +22,14 @@ constexpr int64_t NA_TWO = 256;                   // each half of the two-level 
 constexpr int64_t NA_CHAT = NA_MAX_HALF + 1;      // spectrum C_0..C_n
 constexpr int64_t NA_TOTAL = NA_CHAT + NA_MAX_HALF + NA_TW + 2 * NA_TWO;
 
+constexpr int na_lg(int64_t x) { return x <= 1 ? 0 : 1 + na_lg(x / 2); }
+// the largest tables a series of up to NA_MAX_N needs fit their slots: the
+// single-CTA FP32 product at n = 16384 uses W_n directly, a four-step product
+// W_{n2} with n2 <= n; the two-level W_M table halves are M >> tws and 2^tws
+static_assert(SMALL_MAXE_F32 <= NA_TW && SMALL_MAXE_DF64 <= NA_TW, "direct twiddle slot too small");
+static_assert((NA_MAX_N >> ((na_lg(NA_MAX_N) + 1) / 2)) <= NA_TWO, "two-level table slot too small");
+static_assert(((int64_t)1 << ((na_lg(NA_MAX_N) + 1) / 2)) <= NA_TWO, "two-level table slot too small");
+
 // Shared by every call in the process, on every device that loads the library.
 static __device__ __align__(256) cplx<df64> g_na_scratch[NA_TOTAL];
 
@@ -132,6 +140,8 @@ extern "C" int ssa_matvec_noalloc(const double* f, int64_t N, int64_t L, int tra
   cplx<df64>* tw = Y + NA_MAX_HALF;
   cplx<df64>* tA = tw + NA_TW;
   cplx<df64>* tB = tA + NA_TWO;
+  if (P > NA_TW || nA > NA_TWO || nB > NA_TWO || n > NA_MAX_HALF)
+    return fail(SSA_EINVAL, "ssa_matvec_noalloc: table sizes exceed the fixed scratch layout");
   g.tw = tw;
   g.tA = tA;
   g.tB = tB;

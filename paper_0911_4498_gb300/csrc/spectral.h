@@ -6,6 +6,11 @@
 namespace ssa {
 
 enum { PREC_F64 = 0, PREC_F32C = 1, PREC_NATIVE64 = 2 };
+
+// Largest n = M / 2 of a product run by one CTA in shared memory (128 KB of
+// complex values), per arithmetic type; larger n takes the four-step kernels.
+constexpr int SMALL_MAXE_F32 = 16384;
+constexpr int SMALL_MAXE_DF64 = 8192;
 enum { GATHER_X = 0, GATHER_XT = 1, GATHER_CIRC = 2, GATHER_PAD = 3 };
 enum { ROW_MATVEC = 0, ROW_FWD_STORE = 1, ROW_FWD_MUL_ACC = 2, ROW_INV_LOAD = 3 };
 enum { OUT_SLICE = 0, OUT_HANKEL = 1 };
@@ -74,8 +79,11 @@ bool native_small(const Geom& g);
 // y_j = X x_j in native FP64 with the double spectrum (Rayleigh-quotient refinement)
 void launch_matvec_native(const Geom& g, int transpose, const double* x, int64_t ldx, double* y, int64_t ldy,
                           int batch, const cplx<double>* chat, void* scratch, cudaStream_t s);
+// grouped Hankelization; every output value is multiplied by oscale (a power
+// of two: sigma may be passed scaled into range and the result scaled back)
 void launch_hankel(const Geom& g, int prec, const df64* U, int64_t ldu, const df64* V, int64_t ldv,
                    const double* sigma, const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
-                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, cudaStream_t s);
+                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, double oscale,
+                   cudaStream_t s);
 
 }  // namespace ssa

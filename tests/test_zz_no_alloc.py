@@ -45,7 +45,11 @@ def _noalloc_product(f, L, x, transpose, precision):
     return yd.cpu().numpy()
 
 
-CASES = [(1000, 500, 0), (40000, 13000, 1), (65536, 32768, 0), (777, 600, 1), (65536, 50000, 1)]
+# (30000, *): n = 16384, the largest single-CTA FP32 product, whose direct
+# twiddle table fills its slot of the array exactly; its df64 spectrum takes
+# the four-step kernels with that table
+CASES = [(1000, 500, 0), (40000, 13000, 1), (65536, 32768, 0), (777, 600, 1), (65536, 50000, 1),
+         (30000, 15000, 0), (30000, 20000, 1)]
 
 
 @pytest.mark.parametrize("precision", [ssa.SSA_PREC_F64, ssa.SSA_PREC_F32C])
