@@ -49,7 +49,7 @@ extern "C" {
 #define SSA_EINVAL 1      /* invalid argument (sizes, k, groups, pointers) */
 #define SSA_ENOMEM 2      /* device allocation failed */
 #define SSA_ENOCONV 3     /* Lanczos did not converge within max_restarts; results and residuals are still returned */
-#define SSA_ETIMEOUT 4    /* a bounded device wait ran out (batched / serving front-ends) */
+/* 4 is not used: no kernel of this library waits on another CTA or device, so there is no bounded wait to run out */
 #define SSA_ECUDA 5       /* CUDA runtime error */
 #define SSA_ENUMERIC 6    /* non-finite value met (input or overflow) */
 
@@ -74,6 +74,15 @@ typedef struct ssa_opts {
   int refine;         /* SSA_REFINE_ON: return each sigma_i as the Rayleigh quotient u_i^T X v_i of the
                          returned vectors, computed with native-FP64 FFT products (k extra products);
                          SSA_REFINE_OFF (default): return the Ritz values of the projected matrix */
+  double reorth_skip; /* SSA_PREC_F64 only: skip level tau of the reorthogonalisation ("orthogonalise only
+                         when necessary", section 3.2.2).  0 (default): never skip, every new vector is made
+                         orthogonal to the basis to working precision.  tau > 0: after the first projection
+                         h = Q^T w the rest of the Gram-Schmidt is skipped when w, less its coupling to the
+                         newest column, is orthogonal to the older columns to tau relative (and that coupling
+                         is at most 100 times the rest of w).  1e-12 skips about half of the passes on
+                         well-separated spectra; the basis is then orthogonal only to ~tau, so sigma are
+                         accurate to ~tau sigma_1 absolute and vectors of closely spaced sigma to
+                         ~tau sigma_1 / gap. */
 } ssa_opts_t;
 
 #define SSA_REFINE_OFF 0
@@ -119,8 +128,18 @@ int ssa_matvec(ssa_plan_t plan, int transpose, const double* x, double* y, int n
 /*
  * Truncated SVD step (section 2.2 via section 3): the k leading singular
  * triples of X by Golub-Kahan-Lanczos bidiagonalisation (Algorithm 1) with
- * full reorthogonalisation (classical Gram-Schmidt applied twice, section
- * 3.2.2) and thick restart (section 3.3), every product by Algorithms 2/3.
+ * reorthogonalisation against the whole basis on both sides (section 3.2.2)
+ * and thick restart (section 3.3), every product by Algorithms 2/3.
+ * Reorthogonalisation is classical Gram-Schmidt: in SSA_PREC_F64 the first
+ * projection h = Q^T w; nothing more when max |h_i| <= 1e-12 ||w|| (w is
+ * orthogonal to Q to that level already); otherwise the update fused with a
+ * second projection, and that projection's update only when ||w'||^2 <
+ * ||w||^2 / 2 afterwards (Kahan-Parlett).  In SSA_PREC_F32C one projection
+ * and one update (the FP32 products' own error, ~1e-7 sigma_1, is far above
+ * one pass's double-float orthogonality).
+ * The series is held scaled by an exact power of two (max |f| in [1/2, 1)),
+ * so any finite units work; sigma, residuals and products are returned in
+ * the caller's units.
  * f: N doubles, or NULL to reuse the series given to ssa_set_series.
  * 1 <= k <= min(L, K).  On SSA_OK or SSA_ENOCONV *out holds a new
  * decomposition (free it with ssa_decomp_destroy).
@@ -344,6 +363,17 @@ int ssa_stats_get(ssa_kernel_stat_t* out, int max, int* count);
 
 /* Total kernels launched by the library in this process. */
 uint64_t ssa_kernel_launches(void);
+
+/*
+ * Host-side fault injection for tests of the error paths (not part of the
+ * paper's method): with after >= 0, the next `after` device allocations made
+ * by the single-series calls (ssa_embed_plan, ssa_set_series, ssa_matvec,
+ * ssa_decompose, ssa_reconstruct, ssa_hankelize) succeed and the one after
+ * them fails as if the device were out of memory (no allocator is called),
+ * so that call returns SSA_ENOMEM; the injection then disarms itself.
+ * after < 0 disarms it.  Nothing on the device is made to fail.
+ */
+int ssa_fault_inject_alloc(int64_t after);
 
 /* ---- allocation-free product (no counterpart in the paper) -------------- */
 

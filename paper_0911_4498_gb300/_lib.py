@@ -16,7 +16,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libssa_gb300.so")
 
-SSA_OK, SSA_EINVAL, SSA_ENOMEM, SSA_ENOCONV, SSA_ETIMEOUT, SSA_ECUDA, SSA_ENUMERIC = range(7)
+SSA_OK, SSA_EINVAL, SSA_ENOMEM, SSA_ENOCONV = range(4)
+SSA_ECUDA, SSA_ENUMERIC = 5, 6
 SSA_PREC_F64, SSA_PREC_F32C = 0, 1
 SSA_REFINE_OFF, SSA_REFINE_ON = 0, 1
 
@@ -24,7 +25,7 @@ SSA_REFINE_OFF, SSA_REFINE_ON = 0, 1
 class SsaOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
                 ("krylov_dim", ctypes.c_int), ("keep", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p), ("refine", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("refine", ctypes.c_int), ("reorth_skip", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):
@@ -97,6 +98,7 @@ _SIGS = {
     "ssa_stats_enable": (_I, [_I]),
     "ssa_stats_get": (_I, [ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "ssa_kernel_launches": (ctypes.c_uint64, []),
+    "ssa_fault_inject_alloc": (_I, [_I64]),
     "ssa_strerror": (ctypes.c_char_p, [_I]),
     "ssa_last_error": (ctypes.c_char_p, []),
 }
@@ -152,12 +154,13 @@ def ssa_default_opts() -> SsaOpts:
 
 
 def make_opts(precision=SSA_PREC_F64, tol=0.0, max_restarts=200, krylov_dim=0, keep=0, seed=0, stream=None,
-              refine=SSA_REFINE_OFF):
+              refine=SSA_REFINE_OFF, reorth_skip=0.0):
     o = ssa_default_opts()
     o.precision, o.tol, o.max_restarts = precision, tol, max_restarts
     o.krylov_dim, o.keep, o.seed = krylov_dim, keep, seed
     o.stream = stream
     o.refine = refine
+    o.reorth_skip = reorth_skip
     return o
 
 
@@ -358,6 +361,10 @@ def ssa_stats_get():
 
 def ssa_kernel_launches() -> int:
     return int(lib().ssa_kernel_launches())
+
+
+def ssa_fault_inject_alloc(after: int):
+    _check(lib().ssa_fault_inject_alloc(after))
 
 
 def ssa_strerror(code: int) -> str:

@@ -63,6 +63,7 @@ struct BCtx {
   int nmax;          // largest n of the batch
   int precision;
   double tol;
+  double skip_tau;  // skip level of the gated reorthogonalisation (0: no skip test)
   int max_restarts;
   uint64_t seed;
 };
@@ -152,13 +153,34 @@ SSA_D double circ(const Geom& g, const double* f, int64_t j) {
   return j >= j0 ? f[j - j0] : 0.0;
 }
 
-SSA_D void cta_spectrum(const Geom& g, const double* f, cplx<df64>* chat, cplx<df64>* scr, cplx<df64>* buf) {
+// Exponent e with max |f| = m 2^e, m in [1/2, 1) (0 for a zero series), the
+// same in every thread.  The series enters the double-float spectrum scaled
+// by 2^-e (exact), far from FP32's overflow and underflow whatever its
+// units; sigma and the residuals are scaled back by 2^e at the end.
+SSA_D int cta_series_exp(const double* f, int64_t n) {
+  __shared__ double wm[BT / 32];
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += BT) m = fmax(m, fabs(f[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = wm[0];
+  for (int i = 1; i < BT / 32; ++i) m = fmax(m, wm[i]);
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  return e;
+}
+
+SSA_D void cta_spectrum(const Geom& g, const double* f, double fs, cplx<df64>* chat, cplx<df64>* scr,
+                        cplx<df64>* buf) {
   const int n = 1 << g.lg_n;
   const float s = 0.5f / (4.0f * (float)n);
   const cplx<df64>* Z;
   if (n <= 8192) {
     for (int t = threadIdx.x; t < n; t += BT)
-      buf[t] = mk(df_from_double(circ(g, f, 2 * (int64_t)t)), df_from_double(circ(g, f, 2 * (int64_t)t + 1)));
+      buf[t] = mk(df_from_double(fs * circ(g, f, 2 * (int64_t)t)),
+                  df_from_double(fs * circ(g, f, 2 * (int64_t)t + 1)));
     __syncthreads();
     cta_fft<df64, BT, 8192, false>(buf, g.lg_n, 1, g.tw, g.lg_P);
     Z = buf;
@@ -167,7 +189,7 @@ SSA_D void cta_spectrum(const Geom& g, const double* f, cplx<df64>* chat, cplx<d
     for (int par = 0; par < 2; ++par) {
       for (int t = threadIdx.x; t < h; t += BT) {
         const int64_t j = 4 * (int64_t)t + 2 * par;  // z[2t + par] = c[2(2t+par)] + i c[2(2t+par)+1]
-        buf[t] = mk(df_from_double(circ(g, f, j)), df_from_double(circ(g, f, j + 1)));
+        buf[t] = mk(df_from_double(fs * circ(g, f, j)), df_from_double(fs * circ(g, f, j + 1)));
       }
       __syncthreads();
       cta_fft<df64, BT, 8192, false>(buf, g.lg_n - 1, 1, g.tw, g.lg_P);
@@ -411,14 +433,30 @@ __device__ __noinline__ void cta_cgs_pass(const df64* Q, int64_t ldq, int ncols,
 }
 
 // w <- (I - Q Q^T)^2 w; returns w.w (valid in all threads)
-// mode: REORTH_ONCE (FP32 products) or REORTH_GATED (the third pass only
-// when ||w'||^2 < ||w||^2 / 2 after the first update, Kahan-Parlett).
+// mode: REORTH_ONCE (FP32 products) or REORTH_GATED: after the first
+// projection h, with tau > 0, only w - h_l q_l (l the newest column, whose
+// coefficient is the bidiagonal coupling) when max_{i<l} |h_i| <= tau ||w'|| and
+// ||w||^2 <= SKIP_RATIO ||w'||^2 (the skip test of the single-series
+// engine); else the update with a second projection, and the third pass only
+// when ||w'||^2 < ||w||^2 / 2 after the first update (Kahan-Parlett).
 SSA_D df64 cta_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, df64* h1, df64* h2, df64* scal_,
-                    df64* stbuf, int mode) {
+                    df64* stbuf, int mode, double tau) {
   if (ncols > 0) {
     cta_cgs_pass<false, true>(Q, ldq, ncols, w, dim, nullptr, h1, nullptr, stbuf);
     __syncthreads();
     if (mode == REORTH_GATED) {
+      if (tau > 0.0) {
+        float hm = 0.f;  // every thread reads the same h: a CTA-uniform decision
+        for (int i = 0; i < ncols - 1; ++i) hm = fmaxf(hm, fabsf(h1[i].hi));
+        const double w2 = df_to_double(h1[ncols]), hl = df_to_double(h1[ncols - 1]);
+        const double r2 = w2 - hl * hl;
+        if (r2 > 0.0 && (double)hm * (double)hm <= tau * tau * r2 && w2 <= SKIP_RATIO * r2) {
+          cta_cgs_pass<true, false>(Q + (int64_t)(ncols - 1) * ldq, ldq, 1, w, dim, h1 + (ncols - 1), nullptr,
+                                    scal_, stbuf);
+          __syncthreads();
+          return *scal_;
+        }
+      }
       cta_cgs_pass<true, true>(Q, ldq, ncols, w, dim, h1, h2, nullptr, stbuf);
       __syncthreads();
       if (!df_lt(df_scale(h2[ncols], 2.0f), h1[ncols])) return h2[ncols];
@@ -504,7 +542,8 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
     const uint64_t seed = cx.seed;  // same draws alone and in any batch
     const int reorth = cx.precision == SSA_PREC_F32C ? REORTH_ONCE : REORTH_GATED;
     // spectrum
-    cta_spectrum(g, f, sl.chat, sl.fscr, dbuf);
+    const int fexp = cta_series_exp(f, S.N);
+    cta_spectrum(g, f, ldexp(1.0, -fexp), sl.chat, sl.fscr, dbuf);
     // clear the projected matrix; state
     for (int e = threadIdx.x; e < ldb * ldb; e += BT) sl.B[e] = df_zero();
     if (threadIdx.x == 0) {
@@ -535,7 +574,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
       } else {
         for (int64_t i = threadIdx.x; i < dim; i += BT) w[i] = sm64_uniform_pm1(seed, stream_id, i);
         __syncthreads();
-        const df64 n2 = cta_cgs2(Qb, ldq, ncols, w, dim, h1, h2, &sc_nrm, stbuf, reorth);
+        const df64 n2 = cta_cgs2(Qb, ldq, ncols, w, dim, h1, h2, &sc_nrm, stbuf, reorth, cx.skip_tau);
         const df64 nb = df_sqrt(n2);
         const bool alive = ncols < dim && nb.hi > 1e-6f * sqrtf((float)dim / 3.f);
         const df64 inv = alive ? df_div(make_df(1.f, 0.f), nb) : df_zero();
@@ -553,7 +592,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
     ++stream_id;
     __syncthreads();
     {
-      const df64 n2 = cta_cgs2(U, ldu, 0, sl.y, Lw, h1, h2, &sc_nrm, stbuf, reorth);
+      const df64 n2 = cta_cgs2(U, ldu, 0, sl.y, Lw, h1, h2, &sc_nrm, stbuf, reorth, cx.skip_tau);
       normalize(sl.y, Lw, n2, U, ldu, 0, &sl.T[0]);
     }
     int r = 1, c = 0;
@@ -566,7 +605,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
       df64* bentry = vside ? sl.B + (int64_t)(r - 1) * ldb + c : sl.B + (int64_t)r * ldb + (c - 1);
       cta_matvec<T, MAXE>(g, vside ? 1 : 0, src, sl.y, sl.chat, fbuf);
       ++matvecs;
-      const df64 n2 = cta_cgs2(Qb, ldq, ncols, sl.y, dim, h1, h2, &sc_nrm, stbuf, reorth);
+      const df64 n2 = cta_cgs2(Qb, ldq, ncols, sl.y, dim, h1, h2, &sc_nrm, stbuf, reorth, cx.skip_tau);
       normalize(sl.y, dim, n2, Qb, ldq, ncols, bentry);
       ++stream_id;
       if (vside) ++c;
@@ -669,9 +708,10 @@ __global__ void __launch_bounds__(BT, 1) k_batch_ssa(BCtx cx) {
       const int64_t j = e / S.K, i = e - j * S.K;
       oV[e] = df_to_double(srcV[j * ldsv + i]) * sgn[j];
     }
+    const double unscale = ldexp(1.0, fexp);  // back to the caller's units
     for (int j = threadIdx.x; j < k; j += BT) {
-      cx.out_sigma[S.out_s + j] = sl.sigma_d[j];
-      cx.out_resid[S.out_s + j] = sl.resid[j];
+      cx.out_sigma[S.out_s + j] = sl.sigma_d[j] * unscale;
+      cx.out_resid[S.out_s + j] = sl.resid[j] * unscale;
     }
     if (threadIdx.x == 0) {
       cx.out_info[4 * si + 0] = conv;
@@ -894,12 +934,17 @@ __global__ void __launch_bounds__(BT, 1) k_batch_hankel(BHCtx cx) {
     g.tws = cx.tws;
     g.twshift = cx.lg_Mmax - (S.lg_n + 1);
     const int n = 1 << g.lg_n;
+    // sigma scaled by 2^-e (e of the series' largest sigma) into double-float range, the
+    // output scaled back by 2^e: exact, whatever the units of the series
+    int e = 0;
+    if (cx.sigma[S.out_s] > 0.0) frexp(cx.sigma[S.out_s], &e);
+    const double sg_scale = ldexp(1.0, -e);
     for (int k = threadIdx.x; k <= n; k += BT) acc[k] = mk(df_zero(), df_zero());
     for (int ii = cx.grp_off[grp]; ii < cx.grp_off[grp + 1]; ++ii) {
       const int j = cx.grp_idx[ii];
       const double* u = cx.U + S.out_u + (int64_t)j * S.L;
       const double* v = cx.V + S.out_v + (int64_t)j * S.K;
-      const df64 sg = df_from_double(cx.sigma[S.out_s + j]);
+      const df64 sg = df_from_double(cx.sigma[S.out_s + j] * sg_scale);
       cta_rfft_pad<T, MAXE>(g, u, S.L, buf);
       for (int k = threadIdx.x; k <= n / 2; k += BT) {
         const int nk = (n - k) & (n - 1);
@@ -942,7 +987,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch_hankel(BHCtx cx) {
     __syncthreads();
     cta_fft<T, BT, MAXE, true>(buf, g.lg_n, 1, g.tw, g.lg_P);
     double* o = cx.out + cx.out_off[si] + (int64_t)grp * S.N;
-    const double scale = 1.0 / (8.0 * (double)n);
+    const double scale = ldexp(1.0, e) / (8.0 * (double)n);
     const int64_t mn = S.L < S.K ? S.L : S.K;
     for (int64_t t = threadIdx.x; t < S.N; t += BT) {
       const cplx<T> z = buf[t >> 1];
@@ -1044,6 +1089,7 @@ static int batch_build(int nseries, const int64_t* offsets, const int64_t* Ls, c
   const int64_t nmax_allowed = o.precision == SSA_PREC_F32C ? 32768 : 16384;
   // native-FP64 Rayleigh quotients need N <= 16384 (the double FFT fits one CTA)
   if (o.refine != SSA_REFINE_OFF && o.refine != SSA_REFINE_ON) return bfail(SSA_EINVAL, "unknown refine mode");
+  if (!(o.reorth_skip >= 0.0 && o.reorth_skip < 1e-3)) return bfail(SSA_EINVAL, "reorth_skip must be in [0, 1e-3)");
   const bool refine = o.refine == SSA_REFINE_ON;
   std::vector<int64_t> off, L;
   std::vector<int32_t> kv;
@@ -1207,6 +1253,7 @@ static int batch_build(int nseries, const int64_t* offsets, const int64_t* Ls, c
   cx.ldv = ldv;
   cx.nmax = nmax;
   cx.precision = o.precision;
+  cx.skip_tau = o.precision == SSA_PREC_F32C ? 0.0 : o.reorth_skip;
   cx.tol = o.tol > 0 ? o.tol : (o.precision == SSA_PREC_F32C ? 1e-7 * std::sqrt((double)lgMmax) : 1e-12);
   cx.max_restarts = o.max_restarts;
   cx.seed = o.seed;

@@ -187,5 +187,4 @@ enum : uint32_t {
   SSA_DEV_NONFINITE = 1u,
   SSA_DEV_JACOBI_NOCONV = 2u,
   SSA_DEV_BREAKDOWN = 4u,
-  SSA_DEV_TIMEOUT = 8u,
 };

@@ -59,6 +59,25 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Host-side fault injection for tests (ssa_fault_inject_alloc): when armed
+// with n >= 0, the next n device allocations of this file succeed and the one
+// after them fails as if the device were out of memory, without calling the
+// allocator; then the injection disarms itself.
+static std::atomic<int64_t> g_fail_after{-1};
+template <class T> static cudaError_t dev_alloc(T** ptr, size_t bytes, cudaStream_t s) {
+  int64_t v = g_fail_after.load();
+  while (v >= 0) {
+    if (g_fail_after.compare_exchange_weak(v, v - 1)) {
+      if (v == 0) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMallocAsync(reinterpret_cast<void**>(ptr), bytes, s);
+}
+
 // Device view of a caller buffer: host buffers are staged through a
 // stream-ordered allocation (returned to the pool on release).
 template <class T>
@@ -76,7 +95,7 @@ struct Staged {
       dev = const_cast<T*>(p);
       return SSA_OK;
     }
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&owned), n * sizeof(T) + 16, st));
+    CK(dev_alloc(&owned, n * sizeof(T) + 16, st));
     CK(cudaMemcpyAsync(owned, p, n * sizeof(T), cudaMemcpyHostToDevice, st));
     dev = owned;
     return SSA_OK;
@@ -88,7 +107,7 @@ struct Staged {
       dev = p;
       return SSA_OK;
     }
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&owned), n * sizeof(T) + 16, st));
+    CK(dev_alloc(&owned, n * sizeof(T) + 16, st));
     dev = owned;
     host_dst = p;
     return SSA_OK;
@@ -171,7 +190,7 @@ static void free_async(void* ptr, cudaStream_t s) {
   if (ptr) cudaFreeAsync(ptr, s);
 }
 template <class T> static cudaError_t malloc_async(T** ptr, size_t bytes, cudaStream_t s) {
-  return cudaMallocAsync(reinterpret_cast<void**>(ptr), bytes, s);
+  return dev_alloc(ptr, bytes, s);
 }
 
 // ------------------------------------------------------------------ handles
@@ -204,6 +223,8 @@ struct Workspace {
     free_async(rw.h, st);
     free_async(rw.h2, st);
     free_async(rw.gate, st);
+    free_async(rw.run, st);
+    free_async(rw.skip, st);
     free_async(rw.nrm, st);
     free_async(rw.counter, st);
     free_async(sw.A, st);
@@ -248,6 +269,13 @@ struct ssa_plan_s {
   cplx<double>* tB64 = nullptr;
   cplx<double>* chat64 = nullptr;
   bool has_series = false;
+  // The series is held scaled by 2^-fexp (max |f| in [1/2, 1)), an exact
+  // change of units that keeps every double-float quantity of the method far
+  // from FP32's overflow and underflow; sigma, residuals and products are
+  // scaled back by 2^fexp (U, V do not change, and Hankelization with the
+  // returned sigma is in the caller's units).
+  int fexp = 0;
+  unsigned long long* fstat = nullptr;  // device: [0] max |f| (bits), [1] non-finite count
   Workspace ws;
 };
 
@@ -269,7 +297,7 @@ namespace ssa {
 static const char* const kClassNames[K_NCLASS] = {
     "spectrum", "matvec_small", "matvec_colfwd", "matvec_row", "matvec_colinv", "cgs_proj", "cgs_update",
     "cgs_update_proj", "normalize", "small_svd", "svd_precondition", "ritz", "hankel_small", "hankel_fourstep",
-    "misc", "gated", "batch_ssa"};
+    "misc", "skipped", "batch_ssa"};
 struct PendingLaunch {
   int cls;
   cudaEvent_t a, b;
@@ -377,6 +405,11 @@ extern "C" int ssa_stats_get(ssa_kernel_stat_t* out, int max, int* count) {
 
 extern "C" uint64_t ssa_kernel_launches(void) { return g_launches.load(); }
 
+extern "C" int ssa_fault_inject_alloc(int64_t after) {
+  g_fail_after.store(after < 0 ? -1 : after);
+  return SSA_OK;
+}
+
 extern "C" void ssa_default_opts(ssa_opts_t* o) {
   if (!o) return;
   std::memset(o, 0, sizeof *o);
@@ -388,6 +421,7 @@ extern "C" void ssa_default_opts(ssa_opts_t* o) {
   o->seed = 0;
   o->stream = nullptr;
   o->refine = SSA_REFINE_OFF;
+  o->reorth_skip = 0.0;
 }
 
 extern "C" const char* ssa_strerror(int code) {
@@ -396,7 +430,6 @@ extern "C" const char* ssa_strerror(int code) {
     case SSA_EINVAL: return "invalid argument";
     case SSA_ENOMEM: return "out of device memory";
     case SSA_ENOCONV: return "Lanczos did not converge within max_restarts";
-    case SSA_ETIMEOUT: return "bounded device wait ran out";
     case SSA_ECUDA: return "CUDA error";
     case SSA_ENUMERIC: return "non-finite value";
     default: return "unknown status";
@@ -413,6 +446,7 @@ extern "C" void ssa_plan_destroy(ssa_plan_t p) {
   free_async(p->chat, p->stream);
   free_async(p->scratch, p->stream);
   free_async(p->f_dev, p->stream);
+  free_async(p->fstat, p->stream);
   free_async(p->tw64, p->stream);
   free_async(p->tA64, p->stream);
   free_async(p->tB64, p->stream);
@@ -431,6 +465,7 @@ extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_
   else ssa_default_opts(&o);
   REQ(o.precision == SSA_PREC_F64 || o.precision == SSA_PREC_F32C, "unknown precision %d", o.precision);
   REQ(o.refine == SSA_REFINE_OFF || o.refine == SSA_REFINE_ON, "unknown refine mode %d", o.refine);
+  REQ(o.reorth_skip >= 0.0 && o.reorth_skip < 1e-3, "reorth_skip must be in [0, 1e-3) (got %g)", o.reorth_skip);
   ssa_plan_s* p = new (std::nothrow) ssa_plan_s();
   if (!p) return SSA_ENOMEM;
   p->opts = o;
@@ -480,6 +515,7 @@ extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_
   PK(malloc_async(&p->chat, (n + 1) * sizeof(cplx<df64>), p->stream));
   PK(malloc_async(&p->scratch, spectral_scratch_bytes(g), p->stream));
   PK(malloc_async(&p->f_dev, N * sizeof(double), p->stream));
+  PK(malloc_async(&p->fstat, 2 * sizeof(unsigned long long), p->stream));
   PK(cudaMemcpyAsync(p->tw, htw.data(), P * sizeof(cplx<df64>), cudaMemcpyHostToDevice, p->stream));
   PK(cudaMemcpyAsync(p->tA, hA.data(), nA * sizeof(cplx<df64>), cudaMemcpyHostToDevice, p->stream));
   PK(cudaMemcpyAsync(p->tB, hB.data(), nB * sizeof(cplx<df64>), cudaMemcpyHostToDevice, p->stream));
@@ -517,16 +553,70 @@ extern "C" int ssa_plan_info(ssa_plan_t p, int64_t* M, int* single_cta) {
   return SSA_OK;
 }
 
+// max |f| (as the bits of a non-negative double, which order like integers)
+// and the number of non-finite entries
+__global__ void k_absmax_finite(const double* __restrict__ f, int64_t n, unsigned long long* out) {
+  unsigned long long m = 0ull, bad = 0ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = fabs(f[i]);
+    if (!(a <= 1.7976931348623157e308)) ++bad;  // NaN or infinity
+    else m = max(m, (unsigned long long)__double_as_longlong(a));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (m) atomicMax(out, m);
+    if (bad) atomicAdd(out + 1, bad);
+  }
+}
+// x[i] *= s (s a power of two: exact)
+__global__ void k_scale_d(double* __restrict__ x, int64_t n, double s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= s;
+}
+__global__ void k_scale_copy_d(const double* __restrict__ src, double* __restrict__ dst, int64_t n, double s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i] * s;
+}
+static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(1024, (n + 255) / 256)); }
+static void scale_copy(const double* src, double* dst, int64_t n, int e, cudaStream_t s) {
+  if (e == 0 && src == dst) return;
+  k_scale_copy_d<<<grid_for(n), 256, 0, s>>>(src, dst, n, std::ldexp(1.0, e));
+}
+
 static int set_series(ssa_plan_t p, const double* f) {
+  double fmax = 0.0;
   if (is_device_ptr(f)) {
     CK(cudaMemcpyAsync(p->f_dev, f, p->N * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+    unsigned long long st[2] = {0ull, 0ull};
+    CK(cudaMemsetAsync(p->fstat, 0, sizeof st, p->stream));
+    k_absmax_finite<<<grid_for(p->N), 256, 0, p->stream>>>(p->f_dev, p->N, p->fstat);
+    CHECK_LAUNCH();
+    CK(cudaMemcpyAsync(st, p->fstat, sizeof st, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    if (st[1]) {
+      set_err("f has %llu non-finite entries", st[1]);
+      return SSA_ENUMERIC;
+    }
+    std::memcpy(&fmax, &st[0], sizeof fmax);
   } else {
-    for (int64_t i = 0; i < p->N; ++i)
+    for (int64_t i = 0; i < p->N; ++i) {
       if (!std::isfinite(f[i])) {
         set_err("f[%lld] is not finite", (long long)i);
         return SSA_ENUMERIC;
       }
+      fmax = std::max(fmax, std::fabs(f[i]));
+    }
     CK(cudaMemcpyAsync(p->f_dev, f, p->N * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  }
+  int e = 0;
+  if (fmax > 0.0) std::frexp(fmax, &e);  // fmax = m 2^e, m in [1/2, 1)
+  p->fexp = e;
+  if (e != 0) {
+    k_scale_d<<<grid_for(p->N), 256, 0, p->stream>>>(p->f_dev, p->N, std::ldexp(1.0, -e));
+    CHECK_LAUNCH();
   }
   const float scale = 1.0f / (4.0f * (float)((int64_t)1 << p->g.lg_n));
   launch_spectrum(p->g, p->f_dev, p->chat, p->small ? 1 : 0, scale, p->scratch, p->stream);
@@ -550,7 +640,7 @@ extern "C" int ssa_get_spectrum(ssa_plan_t p, double* re, double* im) {
   std::vector<cplx<df64>> h(n + 1);
   CK(cudaMemcpyAsync(h.data(), p->chat, (n + 1) * sizeof(cplx<df64>), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
-  const double unscale = 4.0 * (double)n;
+  const double unscale = 4.0 * (double)n * std::ldexp(1.0, p->fexp);
   std::vector<double> hre(n + 1), him(n + 1);
   const int64_t n1 = (int64_t)1 << p->g.lg_n1, n2 = (int64_t)1 << p->g.lg_n2;
   for (int64_t k = 0; k <= n; ++k) {
@@ -584,11 +674,15 @@ extern "C" int ssa_matvec(ssa_plan_t p, int transpose, const double* x, double* 
   void* scratch = p->scratch;
   void* tmp = nullptr;
   if (!p->small && nvec > 1) {
-    CK(cudaMallocAsync(&tmp, ((size_t)1 << p->g.lg_n) * sizeof(cplx<df64>) * nvec, p->stream));
+    CK(dev_alloc(&tmp, ((size_t)1 << p->g.lg_n) * sizeof(cplx<df64>) * nvec, p->stream));
     scratch = tmp;
   }
   launch_matvec_d(p->g, p->opts.precision, t, xs.dev, in_len, ys.dev, out_len, nvec, p->chat, scratch, p->stream);
   CHECK_LAUNCH();
+  if (p->fexp) {  // products of the scaled series, back in the caller's units
+    scale_copy(ys.dev, ys.dev, out_len * nvec, p->fexp, p->stream);
+    CHECK_LAUNCH();
+  }
   if (tmp) CK(cudaFreeAsync(tmp, p->stream));
   rc = ys.finish();
   if (rc) return rc;
@@ -625,6 +719,8 @@ static int ensure_workspace(ssa_plan_t p, int d) {
   CK(malloc_async(&w.rw.h, (MAXCOL + 1) * sizeof(df64), st));
   CK(malloc_async(&w.rw.h2, (MAXCOL + 1) * sizeof(df64), st));
   CK(malloc_async(&w.rw.gate, sizeof(int), st));
+  CK(malloc_async(&w.rw.run, sizeof(int), st));
+  CK(malloc_async(&w.rw.skip, sizeof(int), st));
   CK(malloc_async(&w.rw.nrm, sizeof(df64), st));
   CK(malloc_async(&w.rw.counter, sizeof(int), st));
   CK(cudaMemsetAsync(w.rw.counter, 0, sizeof(int), st));
@@ -685,6 +781,7 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   // one reorthogonalisation pass suffices when the products are FP32 (their
   // error, ~1e-7 sigma_1, is far above one pass's df64 orthogonality)
   const int reorth = prec == SSA_PREC_F32C ? REORTH_ONCE : REORTH_GATED;
+  w.rw.skip_tau = prec == SSA_PREC_F32C ? 0.0 : p->opts.reorth_skip;
   launch_cgs2(U, w.ldu, 0, w.y, Lw, w.rw, reorth, s);
   CK((cudaError_t)launch_normalize_coop(w.y, Lw, w.rw, U, w.dummy, w.est, U, w.ldu, 0, seed, stream_id++, w.status,
                                         s));
@@ -732,10 +829,6 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
       set_err("non-finite value in the Lanczos recurrence");
       return SSA_ENUMERIC;
     }
-    if (status & SSA_DEV_TIMEOUT) {
-      set_err("a bounded device wait ran out in the reorthogonalisation");
-      return SSA_ETIMEOUT;
-    }
     if (converged || restarts >= p->opts.max_restarts || kk >= cp) break;
     // thick restart: U <- U P[:, :kk], V <- [V Q[:, :kk], v_{c}], B <- [diag | rho]
     const int nxt = cur ^ 1;
@@ -771,8 +864,8 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
                        cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpy2DAsync(res->Vw, Kw * sizeof(df64), Vf, w.ldv * sizeof(df64), Kw * sizeof(df64), k,
                        cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(res->sigma, w.sw.sigma_d, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(res->resid, w.sw.resid, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  scale_copy(w.sw.sigma_d, res->sigma, k, p->fexp, s);  // back to the caller's units
+  scale_copy(w.sw.resid, res->resid, k, p->fexp, s);
   CHECK_LAUNCH();
   CK(cudaStreamSynchronize(s));
   res->k = k;
@@ -837,13 +930,14 @@ static int refine_sigma(ssa_plan_t p, ssa_decomp_s* res, int k) {
   int chunk = small ? k : (int)std::max<int64_t>(1, std::min<int64_t>(k, ((int64_t)256 << 20) / (n * 16)));
   double* Y = nullptr;
   void* scr = nullptr;
-  CK(cudaMallocAsync(&Y, (size_t)Lw * chunk * sizeof(double), s));
-  if (!small && chunk > 1) CK(cudaMallocAsync(&scr, (size_t)n * chunk * sizeof(cplx<double>), s));
+  CK(dev_alloc(&Y, (size_t)Lw * chunk * sizeof(double), s));
+  if (!small && chunk > 1) CK(dev_alloc(&scr, (size_t)n * chunk * sizeof(cplx<double>), s));
   for (int c0 = 0; c0 < k; c0 += chunk) {
     const int nb = std::min(chunk, k - c0);
     launch_matvec_native(g64, 0, Vi + (int64_t)c0 * Kw, Kw, Y, Lw, nb, p->chat64, scr ? scr : p->scratch, s);
     launch_col_dots(Ui + (int64_t)c0 * Lw, Lw, Y, Lw, Lw, nb, res->sigma + c0, s);
   }
+  scale_copy(res->sigma, res->sigma, k, p->fexp, s);  // products of the scaled series
   CHECK_LAUNCH();
   if (scr) CK(cudaFreeAsync(scr, s));
   CK(cudaFreeAsync(Y, s));
@@ -858,7 +952,7 @@ static int refine_sigma(ssa_plan_t p, ssa_decomp_s* res, int k) {
   std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return sg[a] > sg[b]; });
   auto permute = [&](void* base, size_t colbytes) -> int {
     void* tmp = nullptr;
-    CK(cudaMallocAsync(&tmp, colbytes * k, s));
+    CK(dev_alloc(&tmp, colbytes * k, s));
     CK(cudaMemcpyAsync(tmp, base, colbytes * k, cudaMemcpyDeviceToDevice, s));
     for (int i = 0; i < k; ++i)
       if (perm[i] != i)
@@ -1007,16 +1101,34 @@ static int hankel_common(ssa_plan_t p, const double* sigma_dev, const df64* Uw, 
   if (rc) return rc;
   cudaStream_t s = p->stream;
   int32_t *doff = nullptr, *didx = nullptr;
-  CK(cudaMallocAsync(&doff, (m + 1) * sizeof(int32_t), s));
-  CK(cudaMallocAsync(&didx, hidx.size() * sizeof(int32_t), s));
+  CK(dev_alloc(&doff, (m + 1) * sizeof(int32_t), s));
+  CK(dev_alloc(&didx, hidx.size() * sizeof(int32_t), s));
   CK(cudaMemcpyAsync(doff, hoff.data(), (m + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(didx, hidx.data(), hidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   Staged<double> os;
   rc = os.out(out, (size_t)m * p->N, s);
   if (rc) return rc;
-  launch_hankel(p->g, p->opts.precision, Uw, ldu, Vw, ldv, sigma_dev, doff, didx, hoff.data(), hidx.data(), m,
-                os.dev, p->N, p->scratch, s);
+  // sigma enters the double-float kernels scaled by 2^-e (max sigma in [1/2, 1)) and the result
+  // is scaled back by 2^e: exact, and independent of the units of the series
+  std::vector<double> hs(r);
+  CK(cudaMemcpyAsync(hs.data(), sigma_dev, r * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double smax = 0.0;
+  for (int i = 0; i < r; ++i) {
+    REQ(std::isfinite(hs[i]), "sigma[%d] is not finite", i);
+    smax = std::max(smax, std::fabs(hs[i]));
+  }
+  int e = 0;
+  if (smax > 0.0) std::frexp(smax, &e);
+  double* sig_scaled = nullptr;
+  if (e != 0) {
+    CK(dev_alloc(&sig_scaled, r * sizeof(double), s));
+    scale_copy(sigma_dev, sig_scaled, r, -e, s);
+  }
+  launch_hankel(p->g, p->opts.precision, Uw, ldu, Vw, ldv, sig_scaled ? sig_scaled : sigma_dev, doff, didx,
+                hoff.data(), hidx.data(), m, os.dev, p->N, p->scratch, std::ldexp(1.0, e), s);
   CHECK_LAUNCH();
+  if (sig_scaled) CK(cudaFreeAsync(sig_scaled, s));
   rc = os.finish();
   if (rc) return rc;
   CK(cudaFreeAsync(doff, s));
@@ -1047,8 +1159,8 @@ extern "C" int ssa_hankelize(ssa_plan_t p, const double* sigma, const double* U,
   rc = vs.in(V, (size_t)ldv * (r - 1) + p->K, s);
   if (rc) return rc;
   df64 *Uw = nullptr, *Vw = nullptr;
-  CK(cudaMallocAsync(&Uw, (size_t)p->Lw * r * sizeof(df64), s));
-  CK(cudaMallocAsync(&Vw, (size_t)p->Kw * r * sizeof(df64), s));
+  CK(dev_alloc(&Uw, (size_t)p->Lw * r * sizeof(df64), s));
+  CK(dev_alloc(&Vw, (size_t)p->Kw * r * sizeof(df64), s));
   // working orientation: X^T's left vectors are the user's V when L > K
   const double* uw_src = p->transposed ? vs.dev : us.dev;
   const double* vw_src = p->transposed ? us.dev : vs.dev;

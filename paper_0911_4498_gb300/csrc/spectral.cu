@@ -34,6 +34,13 @@ SSA_D void st(double* p, int64_t i, float v) { p[i] = (double)v; }
 SSA_D void st(double* p, int64_t i, df64 v) { p[i] = df_to_double(v); }
 SSA_D void st(double* p, int64_t i, double v) { p[i] = v; }
 SSA_D void st(df64* p, int64_t i, double v) { p[i] = df_from_double(v); }
+SSA_D double to_d(float v) { return (double)v; }
+SSA_D double to_d(df64 v) { return df_to_double(v); }
+SSA_D double to_d(double v) { return v; }
+// Hankelization output: the value times os, a power of two that brings
+// results computed with sigma scaled into range back to the caller's units
+template <class V> SSA_D void st_os(double* p, int64_t i, V v, double os) { p[i] = to_d(v) * os; }
+template <class V> SSA_D void st_os(df64* p, int64_t i, V v, double os) { st(p, i, to_d(v) * os); }
 
 template <class T, int G, class In>
 SSA_D T gather(const Geom& g, const In* x, int64_t glen, int64_t j) {
@@ -152,7 +159,7 @@ __global__ void __launch_bounds__(THREADS) k_hankel_small(Geom g, const df64* __
                                                           const double* __restrict__ sigma,
                                                           const int* __restrict__ grp_off,
                                                           const int* __restrict__ grp_idx,
-                                                          Out* __restrict__ out, int64_t ldo) {
+                                                          Out* __restrict__ out, int64_t ldo, double oscale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* bu = reinterpret_cast<cplx<T>*>(smem_raw);
   const int n = 1 << g.lg_n;
@@ -214,7 +221,7 @@ __global__ void __launch_bounds__(THREADS) k_hankel_small(Geom g, const df64* __
   for (int64_t t = threadIdx.x; t < g.N; t += THREADS) {
     const cplx<T> z = bu[t >> 1];
     T p = (t & 1) ? z.im : z.re;
-    st(out, t, div_count<T>(mul_scalar<T>(p, scale), cnt_recip_f(g, t)));
+    st_os(out, t, div_count<T>(mul_scalar<T>(p, scale), cnt_recip_f(g, t)), oscale);
   }
 }
 
@@ -346,7 +353,7 @@ __global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict_
 template <class T, int THREADS, int MAXE, int OUTM, class Out>
 __global__ void __launch_bounds__(THREADS) k_fs_col_inv(Geom g, const cplx<T>* __restrict__ Y, Out* __restrict__ y,
                                                         int64_t ldy, int64_t out_off, int64_t out_cnt, float scale,
-                                                        int lg_cb) {
+                                                        int lg_cb, double oscale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int cb = 1 << lg_cb;
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(THREADS) k_fs_col_inv(Geom g, const cplx<T>* _
     if (OUTM == OUT_SLICE) {
       if (i >= out_off && i < out_off + out_cnt) st(y, i - out_off, mul_scalar<T>(v, scale));
     } else {
-      if (i < g.N) st(y, i, div_count<T>(mul_scalar<T>(v, scale), cnt_recip_f(g, i)));
+      if (i < g.N) st_os(y, i, div_count<T>(mul_scalar<T>(v, scale), cnt_recip_f(g, i)), oscale);
     }
   }
 }
@@ -388,9 +395,9 @@ static int lg2(int64_t x) {
 // COLE: elements per CTA of the four-step column kernels (32 KB, 256 threads),
 // small enough for several CTAs per SM and no register spills.
 template <class T> struct Lim;
-template <> struct Lim<float> { static constexpr int MAXE = 16384; static constexpr int COLE = 4096; };
-template <> struct Lim<df64> { static constexpr int MAXE = 8192; static constexpr int COLE = 2048; };
-template <> struct Lim<double> { static constexpr int MAXE = 8192; static constexpr int COLE = 2048; };
+template <> struct Lim<float> { static constexpr int MAXE = SMALL_MAXE_F32; static constexpr int COLE = 4096; };
+template <> struct Lim<df64> { static constexpr int MAXE = SMALL_MAXE_DF64; static constexpr int COLE = 2048; };
+template <> struct Lim<double> { static constexpr int MAXE = SMALL_MAXE_DF64; static constexpr int COLE = 2048; };
 constexpr int TH = 512;
 constexpr int TH_COL = 256;
 constexpr int TH_ROW = 256;
@@ -489,7 +496,7 @@ static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cuda
 
 template <class T, int OUTM, class Out>
 static void fs_inverse(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int64_t off, int64_t cnt, float scale,
-                       int batch, cudaStream_t s, int cls, double bytes, int lg_cb_force = -1) {
+                       int batch, cudaStream_t s, int cls, double bytes, int lg_cb_force = -1, double oscale = 1.0) {
   constexpr int MAXE = Lim<T>::COLE;
   const int lg_cb = lg_cb_force >= 0 ? lg_cb_force : tuned_lg_cb<T>(g, 1);
   const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
@@ -497,7 +504,7 @@ static void fs_inverse(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
   prof_begin(s);
-  kern<<<grid, TH_COL, sm, s>>>(g, Y, y, ldy, off, cnt, scale, lg_cb);
+  kern<<<grid, TH_COL, sm, s>>>(g, Y, y, ldy, off, cnt, scale, lg_cb, oscale);
   prof_end(s, cls, bytes, 5.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n1 * batch, 1);
 }
 
@@ -611,14 +618,14 @@ template <class T, class Out>
 static void hankel_impl(const Geom& g, const df64* U, int64_t ldu, const df64* V, int64_t ldv, const double* sigma,
                         const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
                         const int* grp_idx_host, int m, Out* out, int64_t ldo, void* scratch, bool small,
-                        cudaStream_t s) {
+                        double oscale, cudaStream_t s) {
   if (small) {
     constexpr int MAXE = Lim<T>::MAXE;
     const size_t sm = (size_t)(2 << g.lg_n) * sizeof(cplx<T>);
     auto kern = k_hankel_small<T, TH, MAXE, Out>;
     set_smem(kern, sm);
     prof_begin(s);
-    kern<<<m, TH, sm, s>>>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, out, ldo);
+    kern<<<m, TH, sm, s>>>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, out, ldo, oscale);
     prof_end(s, K_HANKEL_SMALL, 8.0 * (double)(g.L + g.K) * grp_off_host[m] + 8.0 * (double)g.N * m, 0.0);
     return;
   }
@@ -650,22 +657,23 @@ static void hankel_impl(const Geom& g, const df64* U, int64_t ldu, const df64* V
     rc.spec_in = acc;
     fs_row<T, ROW_INV_LOAD>(g, Y, rc, 1, s, K_HANKEL_FS, 0.0);
     fs_inverse<T, OUT_HANKEL, Out>(g, Y, out + (int64_t)grp * ldo, 0, 0, 0, 1.0f / (2.0f * (float)n), 1, s, K_HANKEL_FS,
-                               8.0 * (double)g.N);
+                                   8.0 * (double)g.N, -1, oscale);
   }
 }
 
 void launch_hankel(const Geom& g, int prec, const df64* U, int64_t ldu, const df64* V, int64_t ldv,
                    const double* sigma, const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
-                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, cudaStream_t s) {
+                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, double oscale,
+                   cudaStream_t s) {
   // the small kernel holds two length-n buffers
   if (prec == PREC_F32C) {
     const bool sm = ((int64_t)2 << g.lg_n) <= Lim<float>::MAXE;
     hankel_impl<float, double>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, grp_off_host, grp_idx_host, m,
-                               out, ldo, scratch, sm, s);
+                               out, ldo, scratch, sm, oscale, s);
   } else {
     const bool sm = ((int64_t)2 << g.lg_n) <= Lim<df64>::MAXE;
     hankel_impl<df64, double>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, grp_off_host, grp_idx_host, m, out,
-                              ldo, scratch, sm, s);
+                              ldo, scratch, sm, oscale, s);
   }
 }
 

@@ -152,3 +152,88 @@ def test_rayleigh_refinement(N, L, k):
 def test_bad_refine_mode_rejected():
     with pytest.raises(ssa.SSAError):
         gpu_decompose(synth.three_sines(100, 1), 40, 3, refine=7)
+
+
+@pytest.fixture(scope="module")
+def unit_refs():
+    """Oracle decompositions of the unscaled series (computed once)."""
+    from oracle import fast_hankel
+    out = {}
+    for N, L, k in ((1000, 500, 10), (40000, 13000, 8)):
+        f0 = synth.three_sines(N, seed=N + 1)
+        ref = ossa.decompose(f0, L, k, method="jacobi" if N <= 1500 else "lanczos")
+        chat = fast_hankel.spectrum(f0, L, fast_hankel.fft_length(N), "library")
+        out[N] = (f0, L, k, ref, chat)
+    for n in (800, 3000):
+        f0 = synth.three_sines(n, seed=n)
+        out[("batch", n)] = (f0, ossa.decompose(f0, n // 2, 6, method="jacobi" if n <= 1500 else "lanczos"))
+    return out
+
+
+@pytest.mark.parametrize("scale", [1e25, 1e-25, 1e200, 1e-200])
+def test_series_units_do_not_matter(unit_refs, scale):
+    """Double-float has FP32's exponent range; the library holds the series
+    scaled by an exact power of two, so sigma, products and reconstructions of
+    a series in any units are the unscaled ones times the scale (against the
+    oracle, sigma <= 1e-10, reconstruction <= 1e-9, for a single-CTA and a
+    four-step plan, and in the batched engine)."""
+    from oracle import fast_hankel
+    from ssa_testlib import gpu_matvec
+    for N in (1000, 40000):
+        f0, L, k, ref, chat = unit_refs[N]
+        f = f0 * scale
+        groups = [[0, 1], [2, 3]]
+        got = gpu_decompose_reconstruct(f, L, k, groups)
+        assert got["rc"] == ssa.SSA_OK
+        assert np.max(_rel(got["sigma"], ref["sigma"] * scale)) <= SIG_F64
+        # compared in the series' own units (a norm of 1e200-sized values overflows)
+        rec_ref = ossa.reconstruct(N, L, ref["sigma"], ref["U"], ref["V"], groups, method="fft", fft="library")
+        for g in range(len(groups)):
+            err = np.linalg.norm(got["rec"][g] / scale - rec_ref[g]) / np.linalg.norm(rec_ref[g])
+            assert err <= REC_F64, (N, g, err)
+        # a product of the scaled series is the scaled product
+        K = N - L + 1
+        x = np.random.default_rng(3).standard_normal(K)
+        y = gpu_matvec(f, L, x, 0)[0]
+        want = fast_hankel.hankel_matvec(chat, N, L, x, "library")
+        assert np.max(np.abs(y / scale - want)) <= 1e-13 * np.linalg.norm(f0) * np.linalg.norm(x)
+    # batched engine (one persistent launch), per-series scaling
+    f_a, r_a = unit_refs[("batch", 800)]
+    f_b, r_b = unit_refs[("batch", 3000)]
+    flat = np.concatenate([f_a, f_b]) * scale
+    off = np.array([0, 800, 3800], dtype=np.int64)
+    b, rc = ssa.ssa_decompose_batch(flat, off, np.array([400, 1500], dtype=np.int64),
+                                    np.array([6, 6], dtype=np.int32), ssa.make_opts())
+    try:
+        for j, r in enumerate((r_a, r_b)):
+            sig = np.empty(6)
+            ssa.ssa_batch_get(b, j, sig)
+            assert np.max(_rel(sig, r["sigma"] * scale)) <= SIG_F64
+    finally:
+        ssa.ssa_batch_destroy(b)
+
+
+def test_reorth_skip_option():
+    """The skip test of the reorthogonalisation (opt-in level tau): sigma within 1e-10 of the
+    oracle on a well-separated spectrum, in the single-series and the batched engine; out of
+    range levels are rejected; F32C ignores it (one pass already)."""
+    N, L, k = 5000, 2500, 16
+    f = synth.many_sines(N, seed=11)
+    ref = ossa.decompose(f, L, k, method="lanczos")
+    got = gpu_decompose(f, L, k, reorth_skip=1e-12)
+    assert got["rc"] == ssa.SSA_OK
+    assert np.max(_rel(got["sigma"], ref["sigma"])) <= SIG_F64
+    compare_vectors(got["U"], ref["U"], ref["sigma"], 1e-9, res_tol=1e-11)
+    b, rc = ssa.ssa_decompose_batch(f, np.array([0, N], dtype=np.int64), np.array([L], dtype=np.int64),
+                                    np.array([k], dtype=np.int32), ssa.make_opts(reorth_skip=1e-12))
+    try:
+        sig = np.empty(k)
+        ssa.ssa_batch_get(b, 0, sig)
+        assert np.max(_rel(sig, ref["sigma"])) <= SIG_F64
+    finally:
+        ssa.ssa_batch_destroy(b)
+    for bad in (-1.0, 0.5):
+        with pytest.raises(ssa.SSAError):
+            gpu_decompose(f, L, k, reorth_skip=bad)
+    f32 = gpu_decompose(f, L, k, precision=ssa.SSA_PREC_F32C, reorth_skip=1e-12)
+    assert np.max(_rel(f32["sigma"], ref["sigma"])) <= SIG_F32C
