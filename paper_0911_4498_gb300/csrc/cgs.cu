@@ -84,12 +84,65 @@ __global__ void k_reduce_cols(const df64* __restrict__ part, int ntiles, int ldp
   if (lane == 0) out[col] = s;
 }
 
+// First-pass reduction with the skip test ("orthogonalise only when
+// necessary", section 3.2.2, with the loss measured instead of estimated):
+// out[i] = sum_t part[t][i] for i <= ncols (out[ncols] = ||w||^2).  The
+// product w is not reduced by the recurrence term beforehand, so its
+// coefficient on the newest column, h_l (l = ncols - 1), is the coupling of
+// the bidiagonalisation and is always large; with w' = w - h_l q_l
+// (||w'||^2 ~ ||w||^2 - h_l^2), the last block skips the rest of the
+// Gram-Schmidt when
+//   max_{i<l} |h_i| <= tau ||w'||   (w' already orthogonal to the older columns)
+//   ||w||^2 <= SKIP_RATIO ||w'||^2   (one projection on q_l leaves at most
+//                                     ~1e-14 ||w|| / ||w'|| along it)
+// Then *run = 0 (no update + second projection), *gate = 0 (no third pass)
+// and *skip = 1: the normalisation forms w' itself.  Otherwise *run = 1,
+// *skip = 0.
+__global__ void k_reduce_skip(const df64* __restrict__ part, int ntiles, int ldp, int ncols, df64* __restrict__ out,
+                              int* __restrict__ run, int* __restrict__ gate, int* __restrict__ skip, double tau,
+                              int* __restrict__ counter) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col <= ncols) {
+    df64 s = df_zero();
+    for (int t = lane; t < ntiles; t += 32) s = df_add(s, part[(int64_t)t * ldp + col]);
+    s = warp_sum_df(s);
+    if (lane == 0) out[col] = s;
+  }
+  if (!last_block(counter)) return;
+  __shared__ float wmax[32];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < ncols - 1; i += blockDim.x) {
+    const volatile df64* hp = out + i;
+    m = fmaxf(m, fabsf(hp->hi));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, wmax[i]);
+    const volatile df64* wp = out + ncols;
+    const volatile df64* lp = out + (ncols - 1);
+    const double w2 = df_to_double(make_df(wp->hi, wp->lo));
+    const double hl = df_to_double(make_df(lp->hi, lp->lo));
+    const double r2 = w2 - hl * hl;  // ||w'||^2, good to a few digits when the ratio test passes
+    const double hm = (double)m;
+    const bool skipped = ncols >= 1 && r2 > 0.0 && hm * hm <= tau * tau * r2 && w2 <= SKIP_RATIO * r2;
+    *run = skipped ? 0 : 1;
+    *skip = skipped ? 1 : 0;
+    if (skipped) *gate = 0;
+    *counter = 0;
+  }
+}
+
 // Second-pass reduction: out[i] for i <= ncols (out[ncols] = ||w'||^2), and
 // the Kahan-Parlett decision for the third pass: *gate = ||w'||^2 < ref/2
 // with ref = ||w||^2 before the first update; without a third pass
 // ||w'||^2 is the final squared norm.
 __global__ void k_reduce_gate(const df64* __restrict__ part, int ntiles, int ldp, int ncols, df64* __restrict__ out,
-                              const df64* __restrict__ ref, int* __restrict__ gate, df64* __restrict__ nrm) {
+                              const df64* __restrict__ ref, int* __restrict__ gate, df64* __restrict__ nrm,
+                              const int* flag) {
+  if (flag && *flag == 0) return;
   const int lane = threadIdx.x & 31;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col > ncols) return;
@@ -185,6 +238,19 @@ __global__ void __launch_bounds__(RT) k_cgs_update(const df64* __restrict__ Q, i
 
 
 // ---------------------------------------------------------------- launchers
+// While launch statistics are on, a pass that the device may skip is charged
+// to its class with its bytes only if it runs: the flag is read back first
+// (a synchronisation outside the timed launches).  Without statistics the
+// decision stays on the device.
+static bool flag_on_host(const int* flag, cudaStream_t s) {
+  if (!prof_enabled() || !flag) return true;
+  int v = 1;
+  if (cudaMemcpyAsync(&v, flag, sizeof v, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return true;
+  return v != 0;
+}
+
 constexpr int LNST = 2;  // staged tiles per block: two blocks per SM fit bases up to ~104 columns
 int reorth_blocks(int64_t dim) { return (int)((dim + SLAB - 1) / SLAB); }
 int fused_tiles(int64_t dim) { return (int)((dim + LR - 1) / LR); }
@@ -228,35 +294,50 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
       prof_begin(s);
       lanes_pass<false, true>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, G1, T2, flag, s);
       prof_end(s, K_PROJ, qb + 8.0 * dim, fl);
-      prof_begin(s);
-      k_reduce_cols<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G1, ldp, ncols + 1, rw.h, flag);
-      prof_end(s, K_MISC, 0.0, 0.0);
       if (mode == REORTH_GATED) {
+        const bool skip_test = rw.skip_tau > 0.0;
+        const int* run = skip_test ? rw.run : nullptr;
+        prof_begin(s);
+        if (skip_test)  // the skip test decides on the device whether passes 2 and 3 run
+          k_reduce_skip<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G1, ldp, ncols, rw.h, rw.run, rw.gate, rw.skip,
+                                                        rw.skip_tau, rw.counter);
+        else
+          k_reduce_cols<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G1, ldp, ncols + 1, rw.h, flag);
+        prof_end(s, K_MISC, 0.0, 0.0);
         // pass 2: w <- w - Q h, h2 = Q^T w, ||w||^2; the gate decides on pass 3
         const int G2 = grid(P_UPD_PROJ);
+        const bool ran2 = flag_on_host(run, s);
         prof_begin(s);
-        lanes_pass<true, true>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, G2, T2, flag, s);
-        prof_end(s, K_UPDATE_PROJ, qb + 16.0 * dim, 2 * fl);
+        lanes_pass<true, true>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, G2, T2, run, s);
+        prof_end(s, ran2 ? K_UPDATE_PROJ : K_SKIPPED, ran2 ? qb + 16.0 * dim : 0.0, ran2 ? 2 * fl : 0.0);
         prof_begin(s);
         k_reduce_gate<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G2, ldp, ncols, rw.h2, rw.h + ncols, rw.gate,
-                                                      rw.nrm);
+                                                      rw.nrm, run);
         prof_end(s, K_MISC, 0.0, 0.0);
         hlast = rw.h2;
         gate = rw.gate;
+      } else {
+        prof_begin(s);
+        k_reduce_cols<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G1, ldp, ncols + 1, rw.h, flag);
+        prof_end(s, K_MISC, 0.0, 0.0);
       }
     }
     // last pass: w <- w - Q h, ||w||^2 (skipped on the device when the gate is 0)
     const int G3 = grid(P_UPD);
+    const bool ran3 = gate ? flag_on_host(gate, s) : true;
     prof_begin(s);
     lanes_pass<true, false>(Q, ldq, ncols, w, dim, hlast, rw.part2, ldp, G3, T2, gate, s);
-    prof_end(s, gate ? K_GATED : K_UPDATE, gate ? 0.0 : qb + 16.0 * dim, gate ? 0.0 : fl);
-    // the normalisation adds up the last pass's partial norms (unless the gate skipped that pass)
+    prof_end(s, ran3 ? K_UPDATE : K_SKIPPED, ran3 ? qb + 16.0 * dim : 0.0, ran3 ? fl : 0.0);
+    // the normalisation adds up the last pass's partial norms (unless the gate skipped that pass),
+    // or, when the skip test fired, forms w - h_l q_l and its norm itself
     rw.nrm_blocks = G3;
     rw.nrm_col = ncols;
     rw.nrm_gate = gate;
+    rw.skip_flag = (mode == REORTH_GATED && ncols > 0 && rw.skip_tau > 0.0) ? rw.skip : nullptr;
     return;
   }
   rw.nrm_blocks = 0;
+  rw.skip_flag = nullptr;
   // wide bases: batched passes (four reads of Q)
   prof_begin(s);
   k_cgs_proj<<<G, RT, 0, s>>>(Q, ldq, ncols, w, dim, rw.part, rw.ldp, flag);

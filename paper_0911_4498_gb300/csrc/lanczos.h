@@ -16,6 +16,12 @@ constexpr int SVD_STAGE_MAX = 200 * 1024;  // shared memory for the df64 Jacobi 
 constexpr int SVD_CL = 8;                  // CTAs of the clustered projected-SVD kernel (portable cluster size)
 constexpr int SVD_CL_THREADS = 512;        // threads per CTA of that kernel
 constexpr int FUSED_MAXCOL = 200;   // largest basis for the fused update+projection pass
+// Skip test of the gated reorthogonalisation (when enabled with a level tau):
+// with h = Q^T w from the first projection and w' = w - h_l q_l (l the newest
+// column), the update and the second projection are skipped when
+// max_{i<l} |h_i| <= tau ||w'|| and ||w||^2 <= SKIP_RATIO ||w'||^2 (w' is then
+// orthogonal to Q to that level).
+constexpr double SKIP_RATIO = 1e4;
 
 struct ReorthWork {
   df64* part;    // [blocks][ldp] partial sums (row tiles of SLAB rows)
@@ -25,6 +31,13 @@ struct ReorthWork {
   df64* h;       // projection coefficients of the first pass; h[ncols] = ||w||^2 (MAXCOL + 1)
   df64* h2;      // the same for the second pass; h2[ncols] = ||w'||^2 (MAXCOL + 1)
   int* gate;     // 1 when the third pass must run (Kahan-Parlett test on the device)
+  int* run;      // 1 when the second pass must run (skip test on the device)
+  int* skip;     // 1 when the skip test fired (then *run == 0 and *gate == 0)
+  double skip_tau;  // level of the skip test in REORTH_GATED (0: no skip test)
+  // set by launch_cgs2 for launch_normalize_coop: when *skip_flag is 1 on the
+  // device, the normalisation forms w <- w - h[ncols-1] q_{ncols-1} and its
+  // norm itself (h = the first projection, in h)
+  const int* skip_flag;
   df64* nrm;     // squared norm after the last update (see nrm_blocks)
   // launch_cgs2 may leave the final squared norm as per-block partial sums,
   // column nrm_col of the first nrm_blocks rows of part2, for the following
@@ -53,10 +66,12 @@ void reorth_setup();
 // Classical Gram-Schmidt of w against the ncols columns of Q, then the squared
 // norm ||w||^2 for the next launch_normalize_coop (in *rw.nrm, or as partial
 // sums that it adds up).  REORTH_ONCE: one projection and update (two passes over
-// Q).  REORTH_GATED: a second projection; its update (a third pass) runs only
-// when ||w'||^2 < ||w||^2 / 2 after the first (Kahan-Parlett), so the result
-// is orthogonal to Q to working precision either way.  Bases wider than
-// FUSED_MAXCOL always take both passes.
+// Q).  REORTH_GATED: the first projection h = Q^T w; if rw.skip_tau > 0 and the
+// skip test holds (skip_tau, SKIP_RATIO) only w - h_l q_l remains to form, which the
+// normalisation does; otherwise the update fused with a second projection,
+// and that projection's update (a third pass) only when ||w'||^2 < ||w||^2 / 2
+// after the first (Kahan-Parlett), so the result is orthogonal to Q to
+// working precision.  Bases wider than FUSED_MAXCOL always take two full rounds.
 enum { REORTH_ONCE = 1, REORTH_GATED = 2 };
 void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, int mode,
                  cudaStream_t s);

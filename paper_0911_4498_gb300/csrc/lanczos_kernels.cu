@@ -37,14 +37,36 @@ __global__ void __launch_bounds__(256) k_normalize_coop(df64* __restrict__ w, in
                                                         df64* __restrict__ scratch, int lds, uint64_t seed,
                                                         uint64_t stream, unsigned* status,
                                                         const df64* __restrict__ npart, int nblk, int ldnp,
-                                                        int ncol, const int* ngate) {
+                                                        int ncol, const int* ngate, const int* skipf,
+                                                        const df64* __restrict__ hproj) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   __shared__ df64 sh[32];
   __shared__ df64 hs[MAXCOL + 4];
-  // ||w||^2: *nrm2, or the sum of the reorthogonalisation's per-block partials (npart[b][ncol],
-  // b < nblk; lane-strided then a warp butterfly, the same value in every block)
-  if (threadIdx.x < 32) {
+  if (skipf && *skipf) {
+    // the reorthogonalisation's skip test fired: w <- w - h_l q_l (l = ncols - 1, h_l from
+    // its first projection) and ||w||^2 here, summed over the grid in block order
+    cg::grid_group grid = cg::this_grid();
+    const df64 hl = hproj[ncols - 1];
+    const df64* ql = Q + (int64_t)(ncols - 1) * ldq;
+    df64 a = df_zero();
+    for (int64_t i = tid; i < dim; i += stride) {
+      const df64 x = df_sub(w[i], df_mul(hl, ql[i]));
+      w[i] = x;
+      a = df_fma(x, x, a);
+    }
+    a = block_sum_df(a, sh);
+    if (threadIdx.x == 0) scratch[(int64_t)blockIdx.x * lds + MAXCOL] = a;
+    grid.sync();
+    if (threadIdx.x < 32) {  // lane-strided over the blocks, then a warp butterfly (same sum in every block)
+      df64 t = df_zero();
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t = df_add(t, scratch[(int64_t)b * lds + MAXCOL]);
+      t = warp_sum_df(t);
+      if (threadIdx.x == 0) sh[0] = t;
+    }
+  } else if (threadIdx.x < 32) {
+    // ||w||^2: *nrm2, or the sum of the reorthogonalisation's per-block partials (npart[b][ncol],
+    // b < nblk; lane-strided then a warp butterfly, the same value in every block)
     df64 v;
     if (nblk > 0 && !(ngate && *ngate == 0)) {
       df64 a = df_zero();
@@ -693,8 +715,10 @@ int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64
   const df64* npart = rw.part2;
   int nblk = rw.nrm_blocks, ldnp = rw.ldp2, ncol = rw.nrm_col;
   const int* ngate = rw.nrm_gate;
-  void* args[] = {&w,    &dim,  &nrm,    &qcol,   &bentry, &est,  &Q,    &ldq,  &ncols, &scratch,
-                  &lds,  &seed, &stream, &status, &npart,  &nblk, &ldnp, &ncol, &ngate};
+  const int* skipf = ncols > 0 ? rw.skip_flag : nullptr;
+  const df64* hproj = rw.h;
+  void* args[] = {&w,    &dim,  &nrm,    &qcol,   &bentry, &est,  &Q,    &ldq,  &ncols, &scratch, &lds,
+                  &seed, &stream, &status, &npart,  &nblk, &ldnp, &ncol, &ngate, &skipf, &hproj};
   prof_begin(s);
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_normalize_coop, dim3(blocks), dim3(256), args, 0, s);
   prof_end(s, K_NORMALIZE, 16.0 * dim, 0.0);

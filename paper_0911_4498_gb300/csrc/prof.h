@@ -23,7 +23,7 @@ enum KClass {
   K_HANKEL_SMALL,
   K_HANKEL_FS,
   K_MISC,
-  K_GATED,
+  K_SKIPPED,  // launches of passes that the device decided to skip (no bytes)
   K_BATCH,
   K_NCLASS
 };
