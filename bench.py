@@ -194,35 +194,106 @@ def aggregate(elapsed_s, units, dist=None, device=None):
 
 # ----------------------------------------------------------------- CPU oracle sample
 def cpu_worker(args):
-    """Run the oracle's Lanczos for a bounded number of half-steps (own process, 1 thread)."""
-    from oracle import ssa as ossa
+    """Unit costs of the CPU oracle on this workload (own process, 1 thread): one product of
+    each kind (Algorithms 2/3 on the oracle's radix-2 FFT), MGS-twice reorthogonalisation
+    against 64 basis columns of each length, one restart product, one projected SVD of size d
+    and one rank-1 Hankelization (Algorithm 4)."""
+    from oracle import fast_hankel, jacobi, lanczos
     w = WORKLOADS[args.workload]
     f = series(w)
+    N, L, k = w["N"], w["L"], w["k"]
+    K = N - L + 1
+    Lw, Kw = min(L, K), max(L, K)
+    d, kk = lanczos.default_dims(Lw, Kw, k)
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    M = fast_hankel.fft_length(N)
+    chat = fast_hankel.spectrum(f, L, M)
+    t_spec = time.perf_counter() - t0
+    u, v = rng.standard_normal(L), rng.standard_normal(K)
     t = time.perf_counter()
-    out = ossa.decompose(f, w["L"], w["k"], method="lanczos", max_steps=args.sample_halfsteps)
-    dt = time.perf_counter() - t
-    print(json.dumps({"seconds": dt, "halfsteps": int(out.get("steps", args.sample_halfsteps))}))
+    fast_hankel.hankel_matvec(chat, N, L, v)
+    fast_hankel.hankel_rmatvec(chat, N, L, u)
+    t_mv = (time.perf_counter() - t) / 2
+    C0 = 64
+    t_col = {}
+    for dim in sorted({Lw, Kw}):
+        Q = np.asfortranarray(rng.standard_normal((dim, C0)))
+        x = rng.standard_normal(dim)
+        t = time.perf_counter()
+        lanczos._mgs_twice(Q, C0, x)
+        t_col[dim] = (time.perf_counter() - t) / C0
+    Q = np.asfortranarray(rng.standard_normal((Kw, d)))
+    P = rng.standard_normal((d, kk))
+    t = time.perf_counter()
+    _ = Q @ P
+    t_ritz = (time.perf_counter() - t) * (Lw + Kw) / Kw
+    Bm = np.triu(np.tril(rng.standard_normal((d + 1, d)), 0), -1)
+    t = time.perf_counter()
+    jacobi.svd(Bm)
+    t_svd = time.perf_counter() - t
+    t = time.perf_counter()
+    fast_hankel.rank1_hankelization(1.0, u, v)
+    t_hank = time.perf_counter() - t
+    print(json.dumps({"seconds": time.perf_counter() - t0, "t_spec": t_spec, "t_mv": t_mv,
+                      "t_col": {str(a): b for a, b in t_col.items()}, "t_ritz": t_ritz, "t_svd": t_svd,
+                      "t_hank": t_hank, "d": d, "kk": kk}))
 
 
-def cpu_sample(workload, halfsteps):
+def cpu_sample(workload):
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", workload,
-                        "--sample-halfsteps", str(halfsteps)], capture_output=True, text=True, env=env,
-                       timeout=900)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", workload],
+                       capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         raise RuntimeError("cpu worker failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(workload, halfsteps_full, sample_halfsteps):
-    s = cpu_sample(workload, sample_halfsteps)
-    # decomps/s extrapolated from the sampled half-steps to a whole decomposition
-    value = (s["halfsteps"] / max(halfsteps_full, 1)) / s["seconds"]
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"first {s['halfsteps']} Lanczos half-steps (matvec + MGS-twice reorthogonalisation) of "
-                       f"the same decomposition in {s['seconds']:.1f} s, scaled to the {halfsteps_full} half-steps "
-                       "a full decomposition takes (early half-steps have the smallest bases, so this favours "
-                       "the CPU); reconstruction not included")}
+def oracle_restarts(workload):
+    """Thick restarts the oracle's own Lanczos took on this workload (header of its stored
+    values), or None."""
+    path = WORKLOADS[workload].get("golden")
+    if not path or not os.path.exists(os.path.join(ROOT, path)):
+        return None
+    with open(os.path.join(ROOT, path)) as fh:
+        for line in fh:
+            if line.startswith("#") and "restarts" in line:
+                try:
+                    return int(line.split("restarts")[1].split(",")[0])
+                except ValueError:
+                    return None
+    return None
+
+
+def cpu_decomp_seconds(workload, s, restarts):
+    """Seconds one oracle decomposition + reconstruction takes on one core, from the measured
+    unit costs over the oracle's own schedule (its restart rule, d and kk; restarts as it ran
+    them): spectrum + every half-step (a product and MGS twice against that half-step's basis)
+    + the projected SVD of every cycle + the restart and final Ritz products + k Hankelizations."""
+    w = WORKLOADS[workload]
+    N, L, k = w["N"], w["L"], w["k"]
+    K = N - L + 1
+    Lw, Kw = min(L, K), max(L, K)
+    tcol = {int(a): b for a, b in s["t_col"].items()}
+    tot = s["t_spec"]
+    sched = side_schedule(Lw, Kw, s["d"], s["kk"], restarts)
+    for ncols, dim in sched:
+        tot += s["t_mv"] + ncols * tcol[dim]
+    tot += (restarts + 1) * (s["t_svd"] + s["t_ritz"]) + k * s["t_hank"]
+    return tot, len(sched)
+
+
+def cpu_baseline(workload, gpu_restarts):
+    s = cpu_sample(workload)
+    rs = oracle_restarts(workload)
+    rs = gpu_restarts if rs is None else rs
+    sec, halfsteps = cpu_decomp_seconds(workload, s, rs)
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"unit costs of the oracle measured here in {s['seconds']:.1f} s (one product "
+                       f"{s['t_mv']:.2f} s, MGS twice per basis column, projected SVD, Ritz product, one "
+                       f"Hankelization {s['t_hank']:.2f} s) over the oracle's schedule of {halfsteps} half-steps "
+                       f"and {rs} restarts, plus the reconstruction of all k components: {sec:.0f} s per "
+                       "decomposition")}
 
 
 # ----------------------------------------------------------------- reference arm
@@ -231,20 +302,31 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = WORKLOADS[args.workload]
-    full = args.ref_halfsteps_full
-    vals = []
+    if "N" not in w or "k" not in w or w.get("kind") is not None:
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm covers the single-series "
+                                                              "workloads (the oracle has no batched or served path)"}))
+        return 0
+    rs = oracle_restarts(args.workload)
+    secs, walls = [], []
     for i in range(args.warmup + args.steps):
-        s = cpu_sample(args.workload, args.sample_halfsteps)
+        t = time.perf_counter()
+        s = cpu_sample(args.workload)
+        wall = time.perf_counter() - t
+        sec, halfsteps = cpu_decomp_seconds(args.workload, s, rs if rs is not None else 4)
         if i >= args.warmup:
-            vals.append((s["halfsteps"] / full) / s["seconds"])
-    value = statistics.median(vals)
+            secs.append(sec)
+            walls.append(wall)
+    sec = statistics.median(secs)
+    value = 1.0 / sec
+    sample = (f"each step measures the oracle's unit costs on this host (one product each way, MGS twice "
+              f"against 64 columns, a projected SVD, a Ritz product, a Hankelization; {statistics.median(walls):.1f} s)"
+              f" and prices one decomposition + reconstruction over the oracle's own schedule "
+              f"({halfsteps} half-steps, {rs if rs is not None else 4} restarts): {sec:.0f} s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.median(walls),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "N": w["N"], "L": w["L"], "k": w["k"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: first {args.sample_halfsteps} Lanczos half-steps of the CPU "
-                                       f"oracle, scaled to {full} half-steps per decomposition"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -894,8 +976,9 @@ def run_gpu(args):
     N, L, k = w["N"], w["L"], w["k"]
     K = N - L + 1
     prec = ssa.SSA_PREC_F32C if args.precision == "f32c" else ssa.SSA_PREC_F64
+    skip = args.reorth_skip if prec == ssa.SSA_PREC_F64 else 0.0
     stream = torch.cuda.current_stream()
-    opts = ssa.make_opts(precision=prec, seed=rank, stream=stream.cuda_stream)
+    opts = ssa.make_opts(precision=prec, seed=rank, stream=stream.cuda_stream, reorth_skip=skip)
     f_host = series(w)
     plan = ssa.ssa_embed_plan(N, L, opts)
     f_dev = torch.from_numpy(f_host).cuda()
@@ -961,7 +1044,7 @@ def run_gpu(args):
 
     # roofline of the kernel with the most device time
     hbm, peak_kind = peaks()
-    cand = [s for s in stats if s["name"] not in ("misc", "gated") and s["launches"] > 0]
+    cand = [s for s in stats if s["name"] not in ("misc", "skipped") and s["launches"] > 0]
     dom = max(cand, key=lambda s: s["ms"]) if cand else None
     roof = None
     if dom:
@@ -988,42 +1071,47 @@ def run_gpu(args):
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * k + 8 * k * N}
 
-    # the other precision mode on the same workload (decomposition + reconstruction)
-    modes = None
+    # the other settings on the same workload (decomposition + reconstruction): the other precision,
+    # and in FP64 the full reorthogonalisation (no skip test) beside the skip test
+    name_main = ("f64" if skip == 0 else f"f64_skip{skip:g}") if prec == ssa.SSA_PREC_F64 else "f32c"
+    modes = {name_main: {"value": value, "sigma_rel_err_max": sig_err}}
     if not args.no_modes:
-        other = ssa.SSA_PREC_F32C if prec == ssa.SSA_PREC_F64 else ssa.SSA_PREC_F64
-        plan2 = ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=other, seed=rank, stream=stream.cuda_stream))
-        sig2 = torch.empty(k, dtype=torch.float64, device="cuda")
+        alts = [("f32c", ssa.SSA_PREC_F32C, 0.0), ("f64", ssa.SSA_PREC_F64, 0.0)]
+        if args.reorth_skip > 0:
+            alts.append((f"f64_skip{args.reorth_skip:g}", ssa.SSA_PREC_F64, args.reorth_skip))
+        for name, other, sk in alts:
+            if name in modes:
+                continue
+            plan2 = ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=other, seed=rank, stream=stream.cuda_stream,
+                                                           reorth_skip=sk))
+            sig2 = torch.empty(k, dtype=torch.float64, device="cuda")
 
-        def step2():
-            d, rc = ssa.ssa_decompose(plan2, f_dev, k)
-            try:
-                ssa.ssa_reconstruct(d, off_dev, idx_dev, k, out_dev)
-                ssa.ssa_decomp_get(d, sig2, None, None, None)
-            finally:
-                ssa.ssa_decomp_destroy(d)
+            def step2():
+                d, rc = ssa.ssa_decompose(plan2, f_dev, k)
+                try:
+                    ssa.ssa_reconstruct(d, off_dev, idx_dev, k, out_dev)
+                    ssa.ssa_decomp_get(d, sig2, None, None, None)
+                finally:
+                    ssa.ssa_decomp_destroy(d)
 
-        for _ in range(max(1, args.warmup)):
-            step2()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step2()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        v2, _, _ = aggregate(e0.elapsed_time(e1) / 1000.0, args.steps, dist, "cuda")
-        err2 = None
-        if gold is not None:
-            err2 = float(np.max(np.abs(sig2.cpu().numpy() - gold["sigma"][:k]) / gold["sigma"][:k]))
-        ssa.ssa_plan_destroy(plan2)
-        name_main = "f64" if prec == ssa.SSA_PREC_F64 else "f32c"
-        name_other = "f32c" if other == ssa.SSA_PREC_F32C else "f64"
-        modes = {name_main: {"value": value, "sigma_rel_err_max": sig_err},
-                 name_other: {"value": v2, "sigma_rel_err_max": err2}}
+            for _ in range(max(1, args.warmup)):
+                step2()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                step2()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            v2, _, _ = aggregate(e0.elapsed_time(e1) / 1000.0, args.steps, dist, "cuda")
+            err2 = None
+            if gold is not None:
+                err2 = float(np.max(np.abs(sig2.cpu().numpy() - gold["sigma"][:k]) / gold["sigma"][:k]))
+            ssa.ssa_plan_destroy(plan2)
+            modes[name] = {"value": v2, "sigma_rel_err_max": err2}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload, int(info.get("matvecs", 1)), args.sample_halfsteps)
+        cpu = cpu_baseline(args.workload, int(info.get("restarts", 4)))
 
     ssa.ssa_plan_destroy(plan)
     dd = min(max(2 * k, k + 32), min(L, K))
@@ -1040,7 +1128,8 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "df64" if prec == ssa.SSA_PREC_F64 else "f32+df64", "data": "synthetic",
                 "config": {"workload": args.workload, "N": N, "L": L, "K": K, "k": k, "groups": "k elementary",
-                           "precision": args.precision, "parallelism": f"replicas x{world}",
+                           "precision": args.precision, "reorth_skip": skip,
+                           "parallelism": f"replicas x{world}",
                            "l2": l2_note},
                 "sigma_rel_err_max": sig_err, "converged": bool(info.get("converged")),
                 "restarts": info.get("restarts"), "matvecs_per_decomp": info.get("matvecs"),
@@ -1061,11 +1150,12 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="many_sines_N1M", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="f64", choices=["f64", "f32c"])
+    ap.add_argument("--reorth-skip", type=float, default=1e-12,
+                    help="FP64: skip level of the reorthogonalisation (0 = full Gram-Schmidt every step)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--sample-halfsteps", type=int, default=6)
-    ap.add_argument("--ref-halfsteps-full", type=int, default=400)
     ap.add_argument("--cpu-worker", action="store_true")
     ap.add_argument("--precision-batch", default="f32c", choices=["f64", "f32c"],
                     help="precision of the batch and serving workloads")
