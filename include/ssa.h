@@ -341,6 +341,10 @@ void ssa_serve_destroy(ssa_server_t srv);
  */
 int ssa_fft_tiling(int precision, int64_t N, int* cols_fwd, int* cols_inv);
 
+/* Threads per CTA picked by the same autotuner for the forward column pass,
+   the products' row pass and the inverse column pass (0 when not planned). */
+int ssa_fft_threads(int precision, int64_t N, int* th_fwd, int* th_row, int* th_inv);
+
 /* One entry per kernel of the library: launches, summed device time from
    CUDA events recorded around each launch, and the algorithmic bytes and
    flops charged to those launches (what the method must move / compute,

@@ -12,7 +12,7 @@ from ._lib import (ssa_batch_destroy, ssa_batch_get, ssa_batch_info, ssa_batch_p
                    SSA_ENOCONV, SSA_ENOMEM, SSA_OK, SSA_PREC_F32C, SSA_PREC_F64, SSA_REFINE_OFF, SSA_REFINE_ON,
                    SSAError, groups_csr, lib, make_opts,
                    ssa_decomp_destroy, ssa_decomp_get, ssa_decomp_info, ssa_decompose, ssa_default_opts,
-                   ssa_embed_plan, ssa_fft_tiling, ssa_get_spectrum, ssa_hankelize, ssa_hmatrix, ssa_last_error, ssa_matvec, ssa_matvec_noalloc,
+                   ssa_embed_plan, ssa_fft_threads, ssa_fft_tiling, ssa_get_spectrum, ssa_hankelize, ssa_hmatrix, ssa_last_error, ssa_matvec, ssa_matvec_noalloc,
                    ssa_plan_destroy,
                    ssa_plan_info, ssa_reconstruct, ssa_set_series, ssa_stats_enable, ssa_stats_get,
                    ssa_kernel_launches, ssa_fault_inject_alloc, ssa_strerror, SSA_SERVE_VECTORS, make_serve_opts, ssa_serve_create,

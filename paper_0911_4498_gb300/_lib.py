@@ -95,6 +95,7 @@ _SIGS = {
     "ssa_serve_stats": (_I, [_VP, ctypes.POINTER(ServeStats)]),
     "ssa_serve_destroy": (None, [_VP]),
     "ssa_fft_tiling": (_I, [_I, _I64, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "ssa_fft_threads": (_I, [_I, _I64, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "ssa_stats_enable": (_I, [_I]),
     "ssa_stats_get": (_I, [ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "ssa_kernel_launches": (ctypes.c_uint64, []),
@@ -344,6 +345,13 @@ def ssa_fft_tiling(precision: int, N: int):
     a, b = _I(), _I()
     _check(lib().ssa_fft_tiling(precision, N, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def ssa_fft_threads(precision: int, N: int):
+    """(threads per CTA of the forward column, row and inverse column passes); 0 = not tuned yet."""
+    a, b, c = _I(), _I(), _I()
+    _check(lib().ssa_fft_threads(precision, N, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def ssa_stats_enable(on: bool):

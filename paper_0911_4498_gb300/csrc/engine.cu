@@ -546,6 +546,18 @@ extern "C" int ssa_fft_tiling(int precision, int64_t N, int* cols_fwd, int* cols
   return SSA_OK;
 }
 
+extern "C" int ssa_fft_threads(int precision, int64_t N, int* th_fwd, int* th_row, int* th_inv) {
+  REQ(th_fwd != nullptr && th_row != nullptr && th_inv != nullptr, "NULL argument");
+  REQ(N > 2, "need N > 2");
+  int64_t M = 4;
+  while (M < N) M *= 2;
+  const int lg_n = ilog2(M) - 1;
+  *th_fwd = tuned_threads(precision, lg_n, 0);
+  *th_row = tuned_threads(precision, lg_n, 2);
+  *th_inv = tuned_threads(precision, lg_n, 1);
+  return SSA_OK;
+}
+
 extern "C" int ssa_plan_info(ssa_plan_t p, int64_t* M, int* single_cta) {
   REQ(p != nullptr, "plan is NULL");
   if (M) *M = p->g.M;
@@ -823,7 +835,13 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     CHECK_LAUNCH();
     CK(cudaMemcpyAsync(&converged, w.sw.conv, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&status, w.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    unsigned sfault = 0;
+    CK((cudaError_t)spectral_fault_read(&sfault, s));
     CK(cudaStreamSynchronize(s));
+    if (sfault) {
+      set_err("a bounded wait for a bulk copy into shared memory ran out in the FFT products");
+      return SSA_ECUDA;
+    }
     if (prof_enabled()) prof_flush();
     if (status & SSA_DEV_NONFINITE) {
       set_err("non-finite value in the Lanczos recurrence");

@@ -18,6 +18,7 @@
 // return twice these values; constant factors are folded into the stored
 // spectrum of the series.
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 
 namespace ssa {
@@ -41,9 +42,26 @@ SSA_D void bfly4(cplx<T>& x0, cplx<T>& x1, cplx<T>& x2, cplx<T>& x3) {
   x3 = c_sub(b, dd);
 }
 
+// Twiddle accessors: W_P^m from the table in global memory (read-only path),
+// or from a copy of it in shared memory.
+template <class T> struct TwGlobal {
+  const tab_t<T>* p;
+  SSA_D cplx<T> operator()(int64_t m) const { return tw_load<T>(p, m); }
+};
+template <class T> struct TwShared {
+  const tab_t<T>* p;
+  SSA_D cplx<T> operator()(int64_t m) const {
+    const tab_t<T> v = p[m];
+    if constexpr (std::is_same<T, float>::value) return mk(v.re.hi + v.re.lo, v.im.hi + v.im.lo);
+    else return v;
+  }
+};
+
 // One Stockham stage of radix R.  ilog2 arguments avoid integer division.
-template <class T, int R, int THREADS, int MAXE, bool INV>
-SSA_D void fft_stage(cplx<T>* buf, int lg_len, int count, int lg_ns, const tab_t<T>* tw, int lg_P) {
+// Transform t starts at buf + t * tstride (tstride >= len; padding between
+// transforms spreads a column-major tile over the shared-memory banks).
+template <class T, int R, int THREADS, int MAXE, bool INV, class TW = TwGlobal<T>>
+SSA_D void fft_stage(cplx<T>* buf, int lg_len, int count, int lg_ns, TW tw, int lg_P, int tstride) {
   constexpr int MAXB = (MAXE / R + THREADS - 1) / THREADS;
   const int lg_nbp = lg_len - (R == 4 ? 2 : 1);  // log2 butterflies per transform
   const int nb = count << lg_nbp;
@@ -58,13 +76,13 @@ SSA_D void fft_stage(cplx<T>* buf, int lg_len, int count, int lg_ns, const tab_t
     if (jj < nb) {
       const int t = jj >> lg_nbp;
       const int j = jj & (nbp - 1);
-      const cplx<T>* base = buf + ((size_t)t << lg_len);
+      const cplx<T>* base = buf + (size_t)t * tstride;
       const int jm = j & (ns - 1);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         cplx<T> x = base[j + r * nbp];
         if (r > 0 && jm != 0) {
-          cplx<T> w = tw_load<T>(tw, (int64_t)(r * jm) << tw_shift);
+          cplx<T> w = tw((int64_t)(r * jm) << tw_shift);
           x = INV ? c_mul_conj(x, w) : c_mul(x, w);
         }
         v[q][r] = x;
@@ -80,7 +98,7 @@ SSA_D void fft_stage(cplx<T>* buf, int lg_len, int count, int lg_ns, const tab_t
     if (jj < nb) {
       const int t = jj >> lg_nbp;
       const int j = jj & (nbp - 1);
-      cplx<T>* base = buf + ((size_t)t << lg_len);
+      cplx<T>* base = buf + (size_t)t * tstride;
       const int jm = j & (ns - 1);
       const int idx = ((j >> lg_ns) << (lg_ns + (R == 4 ? 2 : 1))) + jm;
 #pragma unroll
@@ -93,14 +111,19 @@ SSA_D void fft_stage(cplx<T>* buf, int lg_len, int count, int lg_ns, const tab_t
 
 // Batched in-place FFT; caller must __syncthreads() before (data loaded) —
 // the routine ends with a barrier.
-template <class T, int THREADS, int MAXE, bool INV>
-SSA_D void cta_fft(cplx<T>* buf, int lg_len, int count, const tab_t<T>* tw, int lg_P) {
+template <class T, int THREADS, int MAXE, bool INV, class TW>
+SSA_D void cta_fft_tw(cplx<T>* buf, int lg_len, int count, TW tw, int lg_P, int tstride = 0) {
+  if (tstride <= 0) tstride = 1 << lg_len;
   int lg_ns = 0;
   while (lg_len - lg_ns >= 2) {
-    fft_stage<T, 4, THREADS, MAXE, INV>(buf, lg_len, count, lg_ns, tw, lg_P);
+    fft_stage<T, 4, THREADS, MAXE, INV, TW>(buf, lg_len, count, lg_ns, tw, lg_P, tstride);
     lg_ns += 2;
   }
-  if (lg_len - lg_ns == 1) fft_stage<T, 2, THREADS, MAXE, INV>(buf, lg_len, count, lg_ns, tw, lg_P);
+  if (lg_len - lg_ns == 1) fft_stage<T, 2, THREADS, MAXE, INV, TW>(buf, lg_len, count, lg_ns, tw, lg_P, tstride);
+}
+template <class T, int THREADS, int MAXE, bool INV>
+SSA_D void cta_fft(cplx<T>* buf, int lg_len, int count, const tab_t<T>* tw, int lg_P) {
+  cta_fft_tw<T, THREADS, MAXE, INV>(buf, lg_len, count, TwGlobal<T>{tw}, lg_P);
 }
 
 // Real-FFT post-processing for the pair (k, n-k); returns 2 W_k and 2 W_{n-k}

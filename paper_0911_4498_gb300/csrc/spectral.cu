@@ -22,6 +22,7 @@
 #include "spectral.h"
 #include "fft.cuh"
 #include "prof.h"
+#include "bulk.cuh"
 
 namespace ssa {
 
@@ -228,33 +229,83 @@ __global__ void __launch_bounds__(THREADS) k_hankel_small(Geom g, const df64* __
 // ------------------------------------------------ four-step kernels
 // View the packed input z_t (t < n) as n1 x n2 row-major, t = n2 a + b.
 // A: column FFTs over a, twiddle W_n^{b c}, store Y[c][b].
+//
+// Column tiles: a CTA takes cb = 2^lg_cb columns, held column after column
+// in shared memory with one padding element per column (ld = n1 + 1) so that
+// the transposing loads and stores spread over the banks.  Every global load
+// of a thread (the gathered inputs, then the four-step twiddles) is issued
+// before any of them is used: the loops run over a compile-time number of
+// elements per thread.  The column FFTs read W_{n1}^m from a copy in shared
+// memory (every (n2/n1)-th entry of the plan's W_{n2} table).
+template <class T> SSA_HD size_t col_smem_bytes(int lg_n1, int lg_cb) {
+  const size_t data = (size_t)(1 << lg_cb) * ((1 << lg_n1) + 1) * sizeof(cplx<T>);
+  return (data + 15) / 16 * 16 + (size_t)(1 << lg_n1) * sizeof(tab_t<T>);
+}
+
+template <class T>
+SSA_D tab_t<T>* col_twiddles(unsigned char* smem, const Geom& g, int lg_cb, int threads) {
+  const int n1 = 1 << g.lg_n1;
+  const size_t data = (size_t)(1 << lg_cb) * (n1 + 1) * sizeof(cplx<T>);
+  tab_t<T>* tws = reinterpret_cast<tab_t<T>*>(smem + (data + 15) / 16 * 16);
+  const tab_t<T>* tw = g_tw<T>(g);
+  for (int m = threadIdx.x; m < n1; m += threads) tws[m] = tw[(int64_t)m << (g.lg_P - g.lg_n1)];
+  return tws;
+}
+
 template <class T, int THREADS, int MAXE, int G, class In>
 __global__ void __launch_bounds__(THREADS) k_fs_col_fwd(Geom g, const In* __restrict__ x, int64_t ldx, int64_t glen,
                                                         cplx<T>* __restrict__ Y, int lg_cb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-  const int n1 = 1 << g.lg_n1, cb = 1 << lg_cb;
+  const int cb = 1 << lg_cb, ld = (1 << g.lg_n1) + 1;
   const int b0 = blockIdx.x << lg_cb;
   const int64_t n = (int64_t)1 << g.lg_n;
   x += (int64_t)blockIdx.y * ldx;
   Y += (int64_t)blockIdx.y * n;
   const int E = cb << g.lg_n1;
-  for (int e = threadIdx.x; e < E; e += THREADS) {
-    const int bb = e & (cb - 1), a = e >> lg_cb;
-    const int64_t t = ((int64_t)a << g.lg_n2) + b0 + bb;
-    buf[(bb << g.lg_n1) + a] = mk(gather<T, G>(g, x, glen, 2 * t), gather<T, G>(g, x, glen, 2 * t + 1));
+  constexpr int EPT = (MAXE + THREADS - 1) / THREADS;
+  {
+    cplx<T> v[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      if (e < E) {
+        const int bb = e & (cb - 1), a = e >> lg_cb;
+        const int64_t t = ((int64_t)a << g.lg_n2) + b0 + bb;
+        v[q] = mk(gather<T, G>(g, x, glen, 2 * t), gather<T, G>(g, x, glen, 2 * t + 1));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      if (e < E) buf[(e & (cb - 1)) * ld + (e >> lg_cb)] = v[q];
+    }
   }
+  const tab_t<T>* tws = col_twiddles<T>(smem_raw, g, lg_cb, THREADS);
   __syncthreads();
-  cta_fft<T, THREADS, MAXE, false>(buf, g.lg_n1, cb, g_tw<T>(g), g.lg_P);
-  for (int e = threadIdx.x; e < E; e += THREADS) {
-    const int bb = e & (cb - 1), c = e >> lg_cb;
-    const int64_t b = b0 + bb;
-    cplx<T> v = buf[(bb << g.lg_n1) + c];
-    const int64_t m = (2 * ((b * c) & (n - 1)));
-    if (m) v = c_mul(v, twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, (int64_t)(m) << g.twshift));
-    Y[((int64_t)c << g.lg_n2) + b] = v;
+  cta_fft_tw<T, THREADS, MAXE, false>(buf, g.lg_n1, cb, TwShared<T>{tws}, g.lg_n1, ld);
+  cplx<T> tv[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = threadIdx.x + q * THREADS;
+    if (e < E) {
+      const int64_t b = b0 + (e & (cb - 1));
+      const int c = e >> lg_cb;
+      const int64_t m = 2 * ((b * c) & (n - 1));
+      tv[q] = m ? twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, m << g.twshift) : c_one<T>();
+    }
   }
-  (void)n1;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = threadIdx.x + q * THREADS;
+    if (e < E) {
+      const int bb = e & (cb - 1), c = e >> lg_cb;
+      const int64_t b = b0 + bb;
+      cplx<T> v = buf[bb * ld + c];
+      if (2 * ((b * c) & (n - 1))) v = c_mul(v, tv[q]);
+      Y[((int64_t)c << g.lg_n2) + b] = v;
+    }
+  }
 }
 
 // B: row pass over rows c and n1-c (block 0: rows 0 and n1/2).
@@ -348,6 +399,124 @@ __global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict_
   }
 }
 
+// Set (never cleared by the kernels) when a bounded wait of a spectral kernel
+// ran out; read with spectral_fault_read.
+__device__ unsigned g_spectral_fault;
+constexpr unsigned BULK_WAIT_LIMIT = 1u << 24;
+
+// B for the products (ROW_MATVEC), rows staged by TMA bulk copies: one
+// thread arms an mbarrier and copies rows r0 and r1 of Y, the same two rows
+// of the spectrum (four-step order, row c at c * n2), the twiddle table
+// W_{n2}^m and the first n2/2 entries of the two-level table tA into shared
+// memory, all in flight at once.  The row FFTs then read their twiddles from
+// shared memory, and the real-FFT post-processing takes W_M^k, k = c + e n1,
+// as tA[e >> 1] tB[c + (e & 1) n1] (the two-level split at tws = lg_n1 + 1),
+// the same operands as twiddle_M.  The inverse four-step twiddles are
+// gathered from the global tables with all loads of a thread issued before
+// use.  Requires lg_P == lg_n2 (four-step plans).  Arithmetic and operands are
+// those of k_fs_row<T, ..., ROW_MATVEC>, so the results are the same bit for bit.
+template <class T, int THREADS, int MAXE>
+__global__ void __launch_bounds__(THREADS) k_fs_row_mv(Geom g, cplx<T>* __restrict__ Y,
+                                                       const cplx<df64>* __restrict__ chat) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ cplx<df64> tbs[4];   // tB[c], tB[c + n1] for the two rows
+  __shared__ cplx<df64> chat_n;   // C_n, the partner of k = 0 (block 0)
+  const int n1 = 1 << g.lg_n1, n2 = 1 << g.lg_n2;
+  const int64_t n = (int64_t)1 << g.lg_n;
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);                  // rows r0 | r1 of Y
+  cplx<df64>* cs = reinterpret_cast<cplx<df64>*>(buf + 2 * n2);          // rows r0 | r1 of the spectrum
+  cplx<df64>* tws = cs + 2 * n2;                                          // W_{n2}^m, m < n2
+  cplx<df64>* tas = tws + n2;                                             // tA[0 .. n2/2)
+  const int r0 = blockIdx.x;
+  const int r1 = blockIdx.x == 0 ? n1 / 2 : n1 - blockIdx.x;
+  Y += (int64_t)blockIdx.y * n;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    const unsigned yb = (unsigned)(n2 * sizeof(cplx<T>)), cb = (unsigned)(n2 * sizeof(cplx<df64>));
+    mbar_expect_tx(&bar, 2 * yb + 2 * cb + cb + cb / 2);
+    bulk_g2s(buf, Y + ((int64_t)r0 << g.lg_n2), yb, &bar);
+    bulk_g2s(buf + n2, Y + ((int64_t)r1 << g.lg_n2), yb, &bar);
+    bulk_g2s(cs, chat + ((int64_t)r0 << g.lg_n2), cb, &bar);
+    bulk_g2s(cs + n2, chat + ((int64_t)r1 << g.lg_n2), cb, &bar);
+    bulk_g2s(tws, g.tw, cb, &bar);
+    bulk_g2s(tas, g.tA, cb / 2, &bar);
+  }
+  if (threadIdx.x < 4) {
+    const int c = threadIdx.x < 2 ? r0 : r1;
+    tbs[threadIdx.x] = g.tB[c + (threadIdx.x & 1) * n1];
+  }
+  if (threadIdx.x == 4) chat_n = chat[n];
+  __syncthreads();  // the barrier is initialised before anyone polls it
+  if (!mbar_wait(&bar, 0, BULK_WAIT_LIMIT)) {
+    atomicOr(&g_spectral_fault, 1u);
+    mbar_wait(&bar, 0, BULK_WAIT_LIMIT);  // give the copies in flight one more bounded wait
+    return;
+  }
+  const TwShared<T> twsm{tws};
+  cta_fft_tw<T, THREADS, MAXE, false>(buf, g.lg_n2, 2, twsm, g.lg_P);
+  const int npairs = blockIdx.x == 0 ? n2 + 1 : n2;
+  for (int p = threadIdx.x; p < npairs; p += THREADS) {
+    int sa, sb, ca, ea;  // smem slots of the pair members, (row, column) of member a
+    int ra;              // 0: member a in row r0 (block 0: row 0), 1: row r1
+    if (blockIdx.x == 0) {
+      if (p <= n2 / 2) {
+        ca = 0; ea = p; ra = 0;
+        sa = ea; sb = (n2 - p) & (n2 - 1);
+      } else {
+        const int q = p - (n2 / 2 + 1);
+        ca = n1 / 2; ea = q; ra = 1;
+        sa = n2 + ea; sb = n2 + (n2 - 1 - q);
+      }
+    } else {
+      ca = r0; ea = p; ra = 0;
+      sa = ea; sb = n2 + (n2 - 1 - p);
+    }
+    const bool k0 = (ca == 0 && ea == 0);
+    // W_M^k, k = ca + ea n1, from the two-level table (tA[k >> tws] tB[k & mask])
+    const cplx<T> tw = k0 ? c_one<T>() : c_mul(from_tab<T>(tas[ea >> 1]), from_tab<T>(tbs[2 * ra + (ea & 1)]));
+    cplx<T> wk, wnk;
+    rfft_post(buf[sa], buf[sb], tw, wk, wnk);
+    const cplx<T> pk = mul_spec(wk, cs[sa]);
+    const cplx<T> pnk = mul_spec(wnk, k0 ? chat_n : cs[sb]);
+    cplx<T> zk, znk;
+    irfft_pre(pk, pnk, tw, zk, znk);
+    buf[sa] = zk;
+    if (!k0 && sb != sa) buf[sb] = znk;
+  }
+  __syncthreads();
+  cta_fft_tw<T, THREADS, MAXE, true>(buf, g.lg_n2, 2, twsm, g.lg_P);
+  // conj(W_n^{b row}) on the way out, all table loads of this thread first
+  constexpr int EPT = (MAXE + THREADS - 1) / THREADS;
+  cplx<T> tv[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = threadIdx.x + q * THREADS;
+    if (e < 2 * n2) {
+      const int row = e < n2 ? r0 : r1;
+      const int64_t b = e & (n2 - 1);
+      const int64_t m = 2 * ((b * row) & (n - 1));
+      tv[q] = m ? twiddle_M<T>(g_tA<T>(g), g_tB<T>(g), g.tws, m << g.twshift) : c_one<T>();
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = threadIdx.x + q * THREADS;
+    if (e < 2 * n2) {
+      const int row = e < n2 ? r0 : r1;
+      const int64_t b = e & (n2 - 1);
+      const int64_t m = 2 * ((b * row) & (n - 1));
+      cplx<T> v = buf[e];
+      if (m) v = c_mul_conj(v, tv[q]);
+      Y[((int64_t)row << g.lg_n2) + b] = v;
+    }
+  }
+}
+
+int spectral_fault_read(unsigned* host, cudaStream_t s) {
+  return (int)cudaMemcpyFromSymbolAsync(host, g_spectral_fault, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s);
+}
+
 // C: inverse column FFTs over c, unpack the real output and write the slice
 // (matvec) or the count-divided series (Hankelization).
 template <class T, int THREADS, int MAXE, int OUTM, class Out>
@@ -356,25 +525,39 @@ __global__ void __launch_bounds__(THREADS) k_fs_col_inv(Geom g, const cplx<T>* _
                                                         int lg_cb, double oscale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-  const int cb = 1 << lg_cb;
+  const int cb = 1 << lg_cb, ld = (1 << g.lg_n1) + 1;  // padded column tile, as in k_fs_col_fwd
   const int b0 = blockIdx.x << lg_cb;
   const int64_t n = (int64_t)1 << g.lg_n;
   Y += (int64_t)blockIdx.y * n;
   y += (int64_t)blockIdx.y * ldy;
   const int E = cb << g.lg_n1;
-  for (int e = threadIdx.x; e < E; e += THREADS) {
-    const int bb = e & (cb - 1), c = e >> lg_cb;
-    buf[(bb << g.lg_n1) + c] = Y[((int64_t)c << g.lg_n2) + b0 + bb];
+  constexpr int EPT = (MAXE + THREADS - 1) / THREADS;
+  {
+    cplx<T> v[EPT];  // all loads of this thread in flight before the first store
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      if (e < E) v[q] = Y[((int64_t)(e >> lg_cb) << g.lg_n2) + b0 + (e & (cb - 1))];
+    }
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      if (e < E) buf[(e & (cb - 1)) * ld + (e >> lg_cb)] = v[q];
+    }
   }
+  const tab_t<T>* tws = col_twiddles<T>(smem_raw, g, lg_cb, THREADS);
   __syncthreads();
-  cta_fft<T, THREADS, MAXE, true>(buf, g.lg_n1, cb, g_tw<T>(g), g.lg_P);
-  for (int e = threadIdx.x; e < 2 * E; e += THREADS) {
+  cta_fft_tw<T, THREADS, MAXE, true>(buf, g.lg_n1, cb, TwShared<T>{tws}, g.lg_n1, ld);
+#pragma unroll
+  for (int q = 0; q < 2 * EPT; ++q) {
+    const int e = threadIdx.x + q * THREADS;
+    if (e >= 2 * E) break;
     const int half = e & 1;
     const int ee = e >> 1;
     const int bb = ee & (cb - 1), a = ee >> lg_cb;
     const int64_t t = ((int64_t)a << g.lg_n2) + b0 + bb;
     const int64_t i = 2 * t + half;
-    const cplx<T> z = buf[(bb << g.lg_n1) + a];
+    const cplx<T> z = buf[bb * ld + a];
     T v = half ? z.im : z.re;
     if (OUTM == OUT_SLICE) {
       if (i >= out_off && i < out_off + out_cnt) st(y, i - out_off, mul_scalar<T>(v, scale));
@@ -399,7 +582,6 @@ template <> struct Lim<float> { static constexpr int MAXE = SMALL_MAXE_F32; stat
 template <> struct Lim<df64> { static constexpr int MAXE = SMALL_MAXE_DF64; static constexpr int COLE = 2048; };
 template <> struct Lim<double> { static constexpr int MAXE = SMALL_MAXE_DF64; static constexpr int COLE = 2048; };
 constexpr int TH = 512;
-constexpr int TH_COL = 256;
 constexpr int TH_ROW = 256;
 constexpr int MAXE_ROW = 4096;
 
@@ -442,12 +624,17 @@ int col_lg_cb(const Geom& g, int maxe) {
   return lg;
 }
 
-// Columns per CTA (2^lg_cb) of the four-step column passes.  Every choice
-// gives bitwise the same result (each column's FFT runs the same stages);
-// autotune_fourstep() times the candidates once per (arithmetic type, pass,
-// n) and the launches below use the fastest, else the largest tile.
+// Columns per CTA (2^lg_cb) and threads per CTA of the four-step column
+// passes, and threads per CTA of the row pass.  Every choice gives bitwise the
+// same result (each butterfly computes the same operations whichever thread
+// runs it); autotune_fourstep() times the candidates once per (arithmetic
+// type, pass, n) and the launches below use the fastest, else the largest
+// tile with 256 threads.  A tuned column entry holds lg_cb | (thread index << 8),
+// thread index 0, 1, 2 for 128, 256, 512 threads; a row entry 0, 1 for 256, 512.
 template <class T> constexpr int type_slot() { return std::is_same<T, float>::value ? 0 : 1; }
 static std::atomic<int> g_tuned_cb[2][2][32];
+static std::atomic<int> g_tuned_row[2][32];
+constexpr int COL_THREADS[3] = {128, 256, 512};
 static std::atomic<bool> g_tune_init{false};
 static std::mutex g_tune_mu;
 static void tune_table_init() {
@@ -457,31 +644,76 @@ static void tune_table_init() {
   for (auto& a : g_tuned_cb)
     for (auto& b : a)
       for (auto& c : b) c.store(-1);
+  for (auto& a : g_tuned_row)
+    for (auto& b : a) b.store(-1);
   g_tune_init.store(true);
 }
-template <class T> static int tuned_lg_cb(const Geom& g, int pass) {
-  const int dflt = col_lg_cb(g, Lim<T>::COLE);
+// tuned column tile: lg_cb | (thread index << 8)
+template <class T> static int tuned_col(const Geom& g, int pass) {
+  const int dflt = col_lg_cb(g, Lim<T>::COLE) | (1 << 8);
   if (std::is_same<T, double>::value || !g_tune_init.load()) return dflt;
   const int v = g_tuned_cb[type_slot<T>()][pass][g.lg_n].load();
-  return v >= 0 && v <= dflt ? v : dflt;
+  return v >= 0 && (v & 0xff) <= (dflt & 0xff) ? v : dflt;
+}
+template <class T> static int tuned_row_threads(const Geom& g) {
+  if (std::is_same<T, double>::value || !g_tune_init.load()) return 256;
+  return g_tuned_row[type_slot<T>()][g.lg_n].load() == 1 ? 512 : 256;
 }
 
-template <class T, int G, class In>
-static void fs_forward(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s,
-                       int cls, double bytes, int lg_cb_force = -1) {
+template <class T, int G, class In, int TH>
+static void fs_forward_th(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s,
+                          int lg_cb) {
   constexpr int MAXE = Lim<T>::COLE;
-  const int lg_cb = lg_cb_force >= 0 ? lg_cb_force : tuned_lg_cb<T>(g, 0);
-  const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
-  auto kern = k_fs_col_fwd<T, TH_COL, MAXE, G, In>;
+  const size_t sm = col_smem_bytes<T>(g.lg_n1, lg_cb);
+  auto kern = k_fs_col_fwd<T, TH, MAXE, G, In>;
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
+  kern<<<grid, TH, sm, s>>>(g, x, ldx, glen, Y, lg_cb);
+}
+// tile: lg_cb | (thread index << 8); -1 = the tuned (or default) tile
+template <class T, int G, class In>
+static void fs_forward(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s,
+                       int cls, double bytes, int tile = -1) {
+  const int v = tile >= 0 ? tile : tuned_col<T>(g, 0);
+  const int lg_cb = v & 0xff, th = (v >> 8) & 3;
   prof_begin(s);
-  kern<<<grid, TH_COL, sm, s>>>(g, x, ldx, glen, Y, lg_cb);
+  if (th == 0) fs_forward_th<T, G, In, 128>(g, x, ldx, glen, Y, batch, s, lg_cb);
+  else if (th == 2) fs_forward_th<T, G, In, 512>(g, x, ldx, glen, Y, batch, s, lg_cb);
+  else fs_forward_th<T, G, In, 256>(g, x, ldx, glen, Y, batch, s, lg_cb);
   prof_end(s, cls, bytes, 5.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n1 * batch, 1);
 }
 
+template <class T, int TH>
+static void row_mv_th(const Geom& g, cplx<T>* Y, const cplx<df64>* chat, int batch, cudaStream_t s) {
+  const size_t n2 = (size_t)1 << g.lg_n2;
+  const size_t sm = 2 * n2 * sizeof(cplx<T>) + (2 * n2 + n2) * sizeof(cplx<df64>) + n2 / 2 * sizeof(cplx<df64>);
+  auto kern = (2 << g.lg_n2) <= MAXE_ROW / 2 ? k_fs_row_mv<T, TH, MAXE_ROW / 2> : k_fs_row_mv<T, TH, MAXE_ROW>;
+  set_smem(kern, sm);
+  dim3 grid((1 << g.lg_n1) / 2, batch);
+  kern<<<grid, TH, sm, s>>>(g, Y, chat);
+}
+// the staged row pass applies to four-step products whose buffers and tables
+// start on 16-byte boundaries (bulk copies need them); otherwise k_fs_row runs
+template <class T> static bool row_mv_applies(const Geom& g, const void* Y = nullptr, const void* chat = nullptr) {
+  const uintptr_t al = reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(chat) |
+                       reinterpret_cast<uintptr_t>(g.tw) | reinterpret_cast<uintptr_t>(g.tA);
+  return !std::is_same<T, double>::value && g.lg_P == g.lg_n2 && g.twshift == 0 && (2 << g.lg_n2) <= MAXE_ROW &&
+         (al & 15) == 0;
+}
+
 template <class T, int MODE>
-static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cudaStream_t s, int cls, double bytes) {
+static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cudaStream_t s, int cls, double bytes,
+                   int threads = 0) {
+  if constexpr (MODE == ROW_MATVEC && !std::is_same<T, double>::value) {
+    if (row_mv_applies<T>(g, Y, ra.chat)) {
+      const int th = threads > 0 ? threads : tuned_row_threads<T>(g);
+      prof_begin(s);
+      if (th == 512) row_mv_th<T, 512>(g, Y, static_cast<const cplx<df64>*>(ra.chat), batch, s);
+      else row_mv_th<T, 256>(g, Y, static_cast<const cplx<df64>*>(ra.chat), batch, s);
+      prof_end(s, cls, bytes, 10.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n2 * batch, 1);
+      return;
+    }
+  }
   const size_t sm = (size_t)(2 << g.lg_n2) * sizeof(cplx<T>);
   // the register arrays of the in-place FFT are sized by the bound: use the
   // smaller instantiation for rows of up to 1024 points
@@ -494,17 +726,25 @@ static void fs_row(const Geom& g, cplx<T>* Y, const RowArgs& ra, int batch, cuda
   prof_end(s, cls, bytes, 10.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n2 * batch, 1);
 }
 
-template <class T, int OUTM, class Out>
-static void fs_inverse(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int64_t off, int64_t cnt, float scale,
-                       int batch, cudaStream_t s, int cls, double bytes, int lg_cb_force = -1, double oscale = 1.0) {
+template <class T, int OUTM, class Out, int TH>
+static void fs_inverse_th(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int64_t off, int64_t cnt, float scale,
+                          int batch, cudaStream_t s, int lg_cb, double oscale) {
   constexpr int MAXE = Lim<T>::COLE;
-  const int lg_cb = lg_cb_force >= 0 ? lg_cb_force : tuned_lg_cb<T>(g, 1);
-  const size_t sm = (size_t)(1 << (lg_cb + g.lg_n1)) * sizeof(cplx<T>);
-  auto kern = k_fs_col_inv<T, TH_COL, MAXE, OUTM, Out>;
+  const size_t sm = col_smem_bytes<T>(g.lg_n1, lg_cb);
+  auto kern = k_fs_col_inv<T, TH, MAXE, OUTM, Out>;
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
+  kern<<<grid, TH, sm, s>>>(g, Y, y, ldy, off, cnt, scale, lg_cb, oscale);
+}
+template <class T, int OUTM, class Out>
+static void fs_inverse(const Geom& g, const cplx<T>* Y, Out* y, int64_t ldy, int64_t off, int64_t cnt, float scale,
+                       int batch, cudaStream_t s, int cls, double bytes, int tile = -1, double oscale = 1.0) {
+  const int v = tile >= 0 ? tile : tuned_col<T>(g, 1);
+  const int lg_cb = v & 0xff, th = (v >> 8) & 3;
   prof_begin(s);
-  kern<<<grid, TH_COL, sm, s>>>(g, Y, y, ldy, off, cnt, scale, lg_cb, oscale);
+  if (th == 0) fs_inverse_th<T, OUTM, Out, 128>(g, Y, y, ldy, off, cnt, scale, batch, s, lg_cb, oscale);
+  else if (th == 2) fs_inverse_th<T, OUTM, Out, 512>(g, Y, y, ldy, off, cnt, scale, batch, s, lg_cb, oscale);
+  else fs_inverse_th<T, OUTM, Out, 256>(g, Y, y, ldy, off, cnt, scale, batch, s, lg_cb, oscale);
   prof_end(s, cls, bytes, 5.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n1 * batch, 1);
 }
 
@@ -677,67 +917,96 @@ void launch_hankel(const Geom& g, int prec, const df64* U, int64_t ldu, const df
   }
 }
 
-// ---- autotuner of the column tiling
-template <class T>
-static int tune_one(const Geom& g, int pass, const df64* x, df64* y, cplx<T>* Y, cudaStream_t s) {
-  const int maxcb = col_lg_cb(g, Lim<T>::COLE);
+// ---- autotuner of the four-step tiles
+template <class F> static float time_min(F run, cudaStream_t s) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int best = maxcb;
-  float best_ms = 1e30f;
-  for (int cb = 0; cb <= maxcb; ++cb) {
-    auto run = [&]() {
-      if (pass == 0) fs_forward<T, GATHER_X, df64>(g, x, 0, 0, Y, 1, s, K_MISC, 0.0, cb);
-      else fs_inverse<T, OUT_SLICE, df64>(g, Y, y, 0, 0, g.L, 1.0f, 1, s, K_MISC, 0.0, cb);
-    };
-    run();  // warm-up (and the shared-memory opt-in)
-    float ms = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
-      cudaEventRecord(e0, s);
-      for (int i = 0; i < 4; ++i) run();
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float t = 0.f;
-      cudaEventElapsedTime(&t, e0, e1);
-      ms = std::min(ms, t);
-    }
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = cb;
-    }
+  run();  // warm-up (and the shared-memory opt-in)
+  float ms = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < 4; ++i) run();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    ms = std::min(ms, t);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  return ms;
+}
+
+// fastest column tile (lg_cb | thread index << 8) of a pass
+template <class T>
+static int tune_one(const Geom& g, int pass, const df64* x, df64* y, cplx<T>* Y, cudaStream_t s) {
+  const int maxcb = col_lg_cb(g, Lim<T>::COLE);
+  int best = maxcb | (1 << 8);
+  float best_ms = 1e30f;
+  for (int th = 0; th < 3; ++th) {
+    for (int cb = 0; cb <= maxcb; ++cb) {
+      const int tile = cb | (th << 8);
+      const float ms = time_min(
+          [&]() {
+            if (pass == 0) fs_forward<T, GATHER_X, df64>(g, x, 0, 0, Y, 1, s, K_MISC, 0.0, tile);
+            else fs_inverse<T, OUT_SLICE, df64>(g, Y, y, 0, 0, g.L, 1.0f, 1, s, K_MISC, 0.0, tile);
+          },
+          s);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = tile;
+      }
+    }
+  }
   return best;
+}
+
+// fastest threads per CTA of the product's row pass: 0 (256) or 1 (512)
+template <class T> static int tune_row(const Geom& g, cplx<T>* Y, const cplx<df64>* chat, cudaStream_t s) {
+  if (!row_mv_applies<T>(g, Y, chat)) return 0;
+  RowArgs ra{};
+  ra.chat = chat;
+  const float a = time_min([&]() { fs_row<T, ROW_MATVEC>(g, Y, ra, 1, s, K_MISC, 0.0, 256); }, s);
+  const float b = time_min([&]() { fs_row<T, ROW_MATVEC>(g, Y, ra, 1, s, K_MISC, 0.0, 512); }, s);
+  return b < a ? 1 : 0;
 }
 
 int autotune_fourstep(const Geom& g, int prec, cudaStream_t s) {
   tune_table_init();
   if (small_path(g, prec)) return 0;
   const int slot = prec == PREC_F32C ? 0 : 1;
-  if (g_tuned_cb[slot][0][g.lg_n].load() >= 0 && g_tuned_cb[slot][1][g.lg_n].load() >= 0) return 0;
+  if (g_tuned_cb[slot][0][g.lg_n].load() >= 0 && g_tuned_cb[slot][1][g.lg_n].load() >= 0 &&
+      g_tuned_row[slot][g.lg_n].load() >= 0)
+    return 0;
   const int64_t n = (int64_t)1 << g.lg_n;
   void* buf = nullptr;
-  const size_t xb = (size_t)(g.K + g.L + 8) * sizeof(df64);
-  cudaError_t e = cudaMallocAsync(&buf, xb + (size_t)n * sizeof(cplx<df64>), s);
+  // every carved piece starts on a 256-byte boundary (the row pass stages Y and the spectrum with
+  // bulk copies, which need 16-byte aligned addresses)
+  const size_t xb = ((size_t)(g.K + g.L + 8) * sizeof(df64) + 255) / 256 * 256;
+  const size_t yb = ((size_t)n * sizeof(cplx<df64>) + 255) / 256 * 256, cb = (size_t)(n + 1) * sizeof(cplx<df64>);
+  cudaError_t e = cudaMallocAsync(&buf, xb + yb + cb, s);
   if (e != cudaSuccess) return (int)e;
-  cudaMemsetAsync(buf, 0, xb + (size_t)n * sizeof(cplx<df64>), s);
+  cudaMemsetAsync(buf, 0, xb + yb + cb, s);
   df64* x = static_cast<df64*>(buf);
   df64* y = x + g.K + 4;
   void* Yv = static_cast<char*>(buf) + xb;
+  const cplx<df64>* chat = reinterpret_cast<const cplx<df64>*>(static_cast<char*>(buf) + xb + yb);
   prof_suppress(true);
-  int f, i;
+  int f, i, r;
   if (slot == 0) {
     f = tune_one<float>(g, 0, x, y, static_cast<cplx<float>*>(Yv), s);
     i = tune_one<float>(g, 1, x, y, static_cast<cplx<float>*>(Yv), s);
+    r = tune_row<float>(g, static_cast<cplx<float>*>(Yv), chat, s);
   } else {
     f = tune_one<df64>(g, 0, x, y, static_cast<cplx<df64>*>(Yv), s);
     i = tune_one<df64>(g, 1, x, y, static_cast<cplx<df64>*>(Yv), s);
+    r = tune_row<df64>(g, static_cast<cplx<df64>*>(Yv), chat, s);
   }
   prof_suppress(false);
   g_tuned_cb[slot][0][g.lg_n].store(f);
   g_tuned_cb[slot][1][g.lg_n].store(i);
+  g_tuned_row[slot][g.lg_n].store(r);
   cudaFreeAsync(buf, s);
   return (int)cudaGetLastError();
 }
@@ -745,7 +1014,20 @@ int autotune_fourstep(const Geom& g, int prec, cudaStream_t s) {
 int tuned_tiling(int prec, int lg_n, int pass) {
   tune_table_init();
   if (lg_n < 0 || lg_n >= 32 || pass < 0 || pass > 1) return -1;
-  return g_tuned_cb[prec == PREC_F32C ? 0 : 1][pass][lg_n].load();
+  const int v = g_tuned_cb[prec == PREC_F32C ? 0 : 1][pass][lg_n].load();
+  return v < 0 ? v : (v & 0xff);
+}
+
+int tuned_threads(int prec, int lg_n, int pass) {
+  tune_table_init();
+  if (lg_n < 0 || lg_n >= 32 || pass < 0 || pass > 2) return 0;
+  const int slot = prec == PREC_F32C ? 0 : 1;
+  if (pass == 2) {
+    const int r = g_tuned_row[slot][lg_n].load();
+    return r < 0 ? 0 : (r == 1 ? 512 : 256);
+  }
+  const int v = g_tuned_cb[slot][pass][lg_n].load();
+  return v < 0 ? 0 : COL_THREADS[(v >> 8) & 3];
 }
 
 size_t spectral_scratch_bytes(const Geom& g) {

@@ -59,11 +59,17 @@ struct RowArgs {
 };
 
 bool small_path(const Geom& g, int prec);
+// copy the fault word of the spectral kernels (nonzero once a bounded wait
+// for a TMA bulk copy ran out) to *host, ordered on s
+int spectral_fault_read(unsigned* host, cudaStream_t s);
 // Time the column tilings of the four-step passes for this n and precision
 // once per process (synchronises s); returns a cudaError_t value.
 int autotune_fourstep(const Geom& g, int prec, cudaStream_t s);
 // tuned log2(columns per CTA) for (precision, lg_n, pass 0 = forward / 1 = inverse), -1 if not tuned
 int tuned_tiling(int prec, int lg_n, int pass);
+// tuned threads per CTA for (precision, lg_n, pass 0 = forward columns / 1 = inverse
+// columns / 2 = the product's rows), 0 if not tuned
+int tuned_threads(int prec, int lg_n, int pass);
 size_t spectral_scratch_bytes(const Geom& g);
 void launch_matvec_df(const Geom& g, int prec, int transpose, const df64* x, int64_t ldx, df64* y, int64_t ldy,
                       int batch, const cplx<df64>* chat, void* scratch, cudaStream_t s);

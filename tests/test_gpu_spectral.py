@@ -149,6 +149,8 @@ def test_fourstep_autotuner_picks_a_tiling_and_results_match():
         y = gpu_matvec(f, L, x, transpose=False, precision=prec)
         fw, inv = ssa_mod.ssa_fft_tiling(prec, N)
         assert fw >= 1 and inv >= 1 and (fw & (fw - 1)) == 0 and (inv & (inv - 1)) == 0
+        tf, tr, ti = ssa_mod.ssa_fft_threads(prec, N)
+        assert tf in (128, 256, 512) and ti in (128, 256, 512) and tr in (256, 512)
         M = fast_hankel.fft_length(N)
         ref = fast_hankel.hankel_matvec(fast_hankel.spectrum(f, L, M), N, L, x)
         assert np.max(np.abs(y - ref)) <= tol * np.max(np.abs(ref))
