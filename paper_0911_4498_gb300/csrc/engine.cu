@@ -1143,9 +1143,21 @@ static int hankel_common(ssa_plan_t p, const double* sigma_dev, const df64* Uw, 
     CK(dev_alloc(&sig_scaled, r * sizeof(double), s));
     scale_copy(sigma_dev, sig_scaled, r, -e, s);
   }
+  // four-step sizes: scratch for as many groups per launch as fit in 2 GiB, and the per-round index lists
+  const size_t per = hankel_scratch_bytes(p->g, p->opts.precision, 1);
+  int rows = 1;
+  void* hscr = nullptr;
+  int* hidx_dev = nullptr;
+  if (per > 0) {
+    rows = (int)std::max<size_t>(1, std::min<size_t>((size_t)m, ((size_t)2 << 30) / per));
+    CK(dev_alloc(&hscr, hankel_scratch_bytes(p->g, p->opts.precision, rows), s));
+    CK(dev_alloc(&hidx_dev, 2 * std::max<size_t>(1, hidx.size()) * sizeof(int), s));
+  }
   launch_hankel(p->g, p->opts.precision, Uw, ldu, Vw, ldv, sig_scaled ? sig_scaled : sigma_dev, doff, didx,
-                hoff.data(), hidx.data(), m, os.dev, p->N, p->scratch, std::ldexp(1.0, e), s);
+                hoff.data(), hidx.data(), m, os.dev, p->N, hscr, rows, hidx_dev, std::ldexp(1.0, e), s);
   CHECK_LAUNCH();
+  if (hscr) CK(cudaFreeAsync(hscr, s));
+  if (hidx_dev) CK(cudaFreeAsync(hidx_dev, s));
   if (sig_scaled) CK(cudaFreeAsync(sig_scaled, s));
   rc = os.finish();
   if (rc) return rc;

@@ -17,6 +17,8 @@
 //   min(t+1, L, K, N-t) (Algorithm 4 prints a product with the counts; the
 //   convolution identity of section 5 requires the quotient).
 #include <cstdio>
+#include <algorithm>
+#include <vector>
 #include <atomic>
 #include <mutex>
 #include "spectral.h"
@@ -252,15 +254,17 @@ SSA_D tab_t<T>* col_twiddles(unsigned char* smem, const Geom& g, int lg_cb, int 
   return tws;
 }
 
+// col_of_row (may be null): batch row y transforms column col_of_row[y] of x.
 template <class T, int THREADS, int MAXE, int G, class In>
 __global__ void __launch_bounds__(THREADS) k_fs_col_fwd(Geom g, const In* __restrict__ x, int64_t ldx, int64_t glen,
-                                                        cplx<T>* __restrict__ Y, int lg_cb) {
+                                                        cplx<T>* __restrict__ Y, int lg_cb,
+                                                        const int* __restrict__ col_of_row) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int cb = 1 << lg_cb, ld = (1 << g.lg_n1) + 1;
   const int b0 = blockIdx.x << lg_cb;
   const int64_t n = (int64_t)1 << g.lg_n;
-  x += (int64_t)blockIdx.y * ldx;
+  x += (int64_t)(col_of_row ? col_of_row[blockIdx.y] : (int)blockIdx.y) * ldx;
   Y += (int64_t)blockIdx.y * n;
   const int E = cb << g.lg_n1;
   constexpr int EPT = (MAXE + THREADS - 1) / THREADS;
@@ -330,7 +334,8 @@ __global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict_
   using TT = tab_t<T>;
   const TT* chat = static_cast<const TT*>(ra.chat);
   const TT* sin_ = ra.spec_in ? static_cast<const TT*>(ra.spec_in) + (int64_t)blockIdx.y * ra.ld_spec : nullptr;
-  TT* sout = ra.spec_out ? static_cast<TT*>(ra.spec_out) + (int64_t)blockIdx.y * ra.ld_spec : nullptr;
+  const int orow = (MODE == ROW_FWD_MUL_ACC && ra.out_of_row) ? ra.out_of_row[blockIdx.y] : (int)blockIdx.y;
+  TT* sout = ra.spec_out ? static_cast<TT*>(ra.spec_out) + (int64_t)orow * ra.ld_spec : nullptr;
   for (int p = threadIdx.x; p < npairs; p += THREADS) {
     int sa, sb, ca, ea, cbr, eb;  // smem slots and (row, column) of the pair members
     if (blockIdx.x == 0) {
@@ -372,7 +377,8 @@ __global__ void __launch_bounds__(THREADS) k_fs_row(Geom g, cplx<T>* __restrict_
         if (!(k != 0 && sa == sb)) sout[ob] = to_tab<T>(wnk);
         continue;
       } else {  // ROW_FWD_MUL_ACC: spec_out += weight * spec_in * W
-        const T sg = scal<T>::from_double(ra.weight[ra.weight_idx] * 0.5);
+        const int wi = ra.weight_of_row ? ra.weight_of_row[blockIdx.y] : ra.weight_idx;
+        const T sg = scal<T>::from_double(ra.weight[wi] * 0.5);
         cplx<T> qa = c_mul(from_tab<T>(sin_[pa]), wk), qb = c_mul(from_tab<T>(sin_[pb]), wnk);
         qa = mk(s_mul(qa.re, sg), s_mul(qa.im, sg));
         qb = mk(s_mul(qb.re, sg), s_mul(qb.im, sg));
@@ -662,24 +668,24 @@ template <class T> static int tuned_row_threads(const Geom& g) {
 
 template <class T, int G, class In, int TH>
 static void fs_forward_th(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s,
-                          int lg_cb) {
+                          int lg_cb, const int* col_of_row) {
   constexpr int MAXE = Lim<T>::COLE;
   const size_t sm = col_smem_bytes<T>(g.lg_n1, lg_cb);
   auto kern = k_fs_col_fwd<T, TH, MAXE, G, In>;
   set_smem(kern, sm);
   dim3 grid((1 << g.lg_n2) >> lg_cb, batch);
-  kern<<<grid, TH, sm, s>>>(g, x, ldx, glen, Y, lg_cb);
+  kern<<<grid, TH, sm, s>>>(g, x, ldx, glen, Y, lg_cb, col_of_row);
 }
 // tile: lg_cb | (thread index << 8); -1 = the tuned (or default) tile
 template <class T, int G, class In>
 static void fs_forward(const Geom& g, const In* x, int64_t ldx, int64_t glen, cplx<T>* Y, int batch, cudaStream_t s,
-                       int cls, double bytes, int tile = -1) {
+                       int cls, double bytes, int tile = -1, const int* col_of_row = nullptr) {
   const int v = tile >= 0 ? tile : tuned_col<T>(g, 0);
   const int lg_cb = v & 0xff, th = (v >> 8) & 3;
   prof_begin(s);
-  if (th == 0) fs_forward_th<T, G, In, 128>(g, x, ldx, glen, Y, batch, s, lg_cb);
-  else if (th == 2) fs_forward_th<T, G, In, 512>(g, x, ldx, glen, Y, batch, s, lg_cb);
-  else fs_forward_th<T, G, In, 256>(g, x, ldx, glen, Y, batch, s, lg_cb);
+  if (th == 0) fs_forward_th<T, G, In, 128>(g, x, ldx, glen, Y, batch, s, lg_cb, col_of_row);
+  else if (th == 2) fs_forward_th<T, G, In, 512>(g, x, ldx, glen, Y, batch, s, lg_cb, col_of_row);
+  else fs_forward_th<T, G, In, 256>(g, x, ldx, glen, Y, batch, s, lg_cb, col_of_row);
   prof_end(s, cls, bytes, 5.0 * (double)((int64_t)1 << g.lg_n) * g.lg_n1 * batch, 1);
 }
 
@@ -857,8 +863,8 @@ void launch_spectrum64(const Geom& g, const double* f, cplx<double>* chat, int n
 template <class T, class Out>
 static void hankel_impl(const Geom& g, const df64* U, int64_t ldu, const df64* V, int64_t ldv, const double* sigma,
                         const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
-                        const int* grp_idx_host, int m, Out* out, int64_t ldo, void* scratch, bool small,
-                        double oscale, cudaStream_t s) {
+                        const int* grp_idx_host, int m, Out* out, int64_t ldo, void* scratch, int rows,
+                        int* dev_idx, bool small, double oscale, cudaStream_t s) {
   if (small) {
     constexpr int MAXE = Lim<T>::MAXE;
     const size_t sm = (size_t)(2 << g.lg_n) * sizeof(cplx<T>);
@@ -869,51 +875,105 @@ static void hankel_impl(const Geom& g, const df64* U, int64_t ldu, const df64* V
     prof_end(s, K_HANKEL_SMALL, 8.0 * (double)(g.L + g.K) * grp_off_host[m] + 8.0 * (double)g.N * m, 0.0);
     return;
   }
-  // large M: per component, forward FFT of u' (stored), forward FFT of v'
-  // multiplied into the group's accumulator; then one inverse per group.
+  // Large M.  Groups in chunks of `rows`; within a chunk the components go in
+  // rounds, round r holding the r-th member of every group that has one, so no
+  // two batch rows of a launch add into the same accumulator.  Per round: the
+  // forward FFTs of all its u' (spectra stored) and of all its v' (multiplied by
+  // sigma and the stored u spectrum into the groups' accumulators), one launch
+  // each; per chunk: one inverse of all its groups.
   const int64_t n = (int64_t)1 << g.lg_n;
-  cplx<T>* Y = reinterpret_cast<cplx<T>*>(scratch);
-  cplx<df64>* su = reinterpret_cast<cplx<df64>*>(reinterpret_cast<char*>(scratch) + n * sizeof(cplx<df64>));
-  cplx<df64>* acc = su + (n + 1);
-  for (int grp = 0; grp < m; ++grp) {
-    cudaMemsetAsync(acc, 0, (n + 1) * sizeof(cplx<df64>), s);
-    for (int ii = grp_off_host[grp]; ii < grp_off_host[grp + 1]; ++ii) {
-      const int comp = grp_idx_host[ii];
-      fs_forward<T, GATHER_PAD, df64>(g, U + (int64_t)comp * ldu, 0, g.L, Y, 1, s, K_HANKEL_FS, 8.0 * g.L);
-      RowArgs ra{};
-      ra.spec_out = su;
-      ra.natural = 0;
-      ra.scale = 1.0f;
-      fs_row<T, ROW_FWD_STORE>(g, Y, ra, 1, s, K_HANKEL_FS, 0.0);
-      fs_forward<T, GATHER_PAD, df64>(g, V + (int64_t)comp * ldv, 0, g.K, Y, 1, s, K_HANKEL_FS, 8.0 * g.K);
-      RowArgs rb{};
-      rb.spec_in = su;
-      rb.spec_out = acc;
-      rb.weight = sigma;
-      rb.weight_idx = comp;
-      fs_row<T, ROW_FWD_MUL_ACC>(g, Y, rb, 1, s, K_HANKEL_FS, 0.0);
+  const int R = rows < 1 ? 1 : rows;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  char* base = static_cast<char*>(scratch);
+  cplx<T>* Y = reinterpret_cast<cplx<T>*>(base);
+  cplx<df64>* su = reinterpret_cast<cplx<df64>*>(base + al((size_t)R * n * sizeof(cplx<T>)));
+  cplx<df64>* acc = reinterpret_cast<cplx<df64>*>(reinterpret_cast<char*>(su) + al((size_t)R * (n + 1) * 16));
+  // host list of (component, accumulator row) per round, uploaded once
+  std::vector<int> idx;
+  struct Round { int g0, gc, off, b; };
+  std::vector<Round> plan;
+  for (int g0 = 0; g0 < m; g0 += R) {
+    const int gc = std::min(R, m - g0);
+    int maxsz = 0;
+    for (int gg = g0; gg < g0 + gc; ++gg) maxsz = std::max(maxsz, grp_off_host[gg + 1] - grp_off_host[gg]);
+    if (maxsz == 0) {  // only empty groups: their reconstructions are zero
+      for (int gg = g0; gg < g0 + gc; ++gg) cudaMemsetAsync(out + (int64_t)gg * ldo, 0, (size_t)g.N * sizeof(Out), s);
+      continue;
     }
-    RowArgs rc{};
-    rc.spec_in = acc;
-    fs_row<T, ROW_INV_LOAD>(g, Y, rc, 1, s, K_HANKEL_FS, 0.0);
-    fs_inverse<T, OUT_HANKEL, Out>(g, Y, out + (int64_t)grp * ldo, 0, 0, 0, 1.0f / (2.0f * (float)n), 1, s, K_HANKEL_FS,
-                                   8.0 * (double)g.N, -1, oscale);
+    plan.push_back({g0, gc, -1, 0});  // chunk marker (b = 0): clear, then rounds, then the inverse
+    for (int r = 0; r < maxsz; ++r) {
+      Round rd{g0, gc, (int)idx.size(), 0};
+      std::vector<int> comps, accs;
+      for (int gg = g0; gg < g0 + gc; ++gg)
+        if (grp_off_host[gg + 1] - grp_off_host[gg] > r) {
+          comps.push_back(grp_idx_host[grp_off_host[gg] + r]);
+          accs.push_back(gg - g0);
+        }
+      rd.b = (int)comps.size();
+      idx.insert(idx.end(), comps.begin(), comps.end());
+      idx.insert(idx.end(), accs.begin(), accs.end());
+      plan.push_back(rd);
+    }
   }
+  if (!idx.empty()) cudaMemcpyAsync(dev_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  for (size_t i = 0; i < plan.size(); ++i) {
+    const Round& rd = plan[i];
+    if (rd.b == 0) {
+      cudaMemsetAsync(acc, 0, (size_t)rd.gc * (n + 1) * sizeof(cplx<df64>), s);
+      continue;
+    }
+    const int* dcomp = dev_idx + rd.off;
+    const int* dacc = dcomp + rd.b;
+    fs_forward<T, GATHER_PAD, df64>(g, U, ldu, g.L, Y, rd.b, s, K_HANKEL_FS, 8.0 * g.L * rd.b, -1, dcomp);
+    RowArgs ra{};
+    ra.spec_out = su;
+    ra.ld_spec = n + 1;
+    ra.natural = 0;
+    ra.scale = 1.0f;
+    fs_row<T, ROW_FWD_STORE>(g, Y, ra, rd.b, s, K_HANKEL_FS, 0.0);
+    fs_forward<T, GATHER_PAD, df64>(g, V, ldv, g.K, Y, rd.b, s, K_HANKEL_FS, 8.0 * g.K * rd.b, -1, dcomp);
+    RowArgs rb{};
+    rb.spec_in = su;
+    rb.spec_out = acc;
+    rb.ld_spec = n + 1;
+    rb.weight = sigma;
+    rb.weight_of_row = dcomp;
+    rb.out_of_row = dacc;
+    fs_row<T, ROW_FWD_MUL_ACC>(g, Y, rb, rd.b, s, K_HANKEL_FS, 0.0);
+    const bool last_round = i + 1 == plan.size() || plan[i + 1].b == 0;
+    if (last_round) {
+      RowArgs rc{};
+      rc.spec_in = acc;
+      rc.ld_spec = n + 1;
+      fs_row<T, ROW_INV_LOAD>(g, Y, rc, rd.gc, s, K_HANKEL_FS, 0.0);
+      fs_inverse<T, OUT_HANKEL, Out>(g, Y, out + (int64_t)rd.g0 * ldo, ldo, 0, 0, 1.0f / (2.0f * (float)n), rd.gc, s,
+                                     K_HANKEL_FS, 8.0 * (double)g.N * rd.gc, -1, oscale);
+    }
+  }
+}
+
+size_t hankel_scratch_bytes(const Geom& g, int prec, int rows) {
+  const int64_t n = (int64_t)1 << g.lg_n;
+  const bool f32 = prec == PREC_F32C;
+  if (((int64_t)2 << g.lg_n) <= (f32 ? Lim<float>::MAXE : Lim<df64>::MAXE)) return 0;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t R = rows < 1 ? 1 : rows;
+  return al(R * n * (f32 ? sizeof(cplx<float>) : sizeof(cplx<df64>))) + al(R * (n + 1) * 16) + R * (n + 1) * 16;
 }
 
 void launch_hankel(const Geom& g, int prec, const df64* U, int64_t ldu, const df64* V, int64_t ldv,
                    const double* sigma, const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
-                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, double oscale,
-                   cudaStream_t s) {
+                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, int rows, int* dev_idx,
+                   double oscale, cudaStream_t s) {
   // the small kernel holds two length-n buffers
   if (prec == PREC_F32C) {
     const bool sm = ((int64_t)2 << g.lg_n) <= Lim<float>::MAXE;
     hankel_impl<float, double>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, grp_off_host, grp_idx_host, m,
-                               out, ldo, scratch, sm, oscale, s);
+                               out, ldo, scratch, rows, dev_idx, sm, oscale, s);
   } else {
     const bool sm = ((int64_t)2 << g.lg_n) <= Lim<df64>::MAXE;
     hankel_impl<df64, double>(g, U, ldu, V, ldv, sigma, grp_off_dev, grp_idx_dev, grp_off_host, grp_idx_host, m, out,
-                              ldo, scratch, sm, oscale, s);
+                              ldo, scratch, rows, dev_idx, sm, oscale, s);
   }
 }
 

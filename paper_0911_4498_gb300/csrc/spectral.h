@@ -56,6 +56,10 @@ struct RowArgs {
   float scale;                 // ROW_FWD_STORE: multiply W by this power of two
   const double* weight;        // ROW_FWD_MUL_ACC: sigma array on the device
   int weight_idx;
+  // ROW_FWD_MUL_ACC over a batch: per batch row y, the weight index (component)
+  // and the spec_out row (group accumulator); null: weight_idx and row y
+  const int* weight_of_row;
+  const int* out_of_row;
 };
 
 bool small_path(const Geom& g, int prec);
@@ -85,11 +89,17 @@ bool native_small(const Geom& g);
 // y_j = X x_j in native FP64 with the double spectrum (Rayleigh-quotient refinement)
 void launch_matvec_native(const Geom& g, int transpose, const double* x, int64_t ldx, double* y, int64_t ldy,
                           int batch, const cplx<double>* chat, void* scratch, cudaStream_t s);
-// grouped Hankelization; every output value is multiplied by oscale (a power
-// of two: sigma may be passed scaled into range and the result scaled back)
+// Grouped Hankelization; every output value is multiplied by oscale (a power
+// of two: sigma may be passed scaled into range and the result scaled back).
+// Four-step sizes transform the components of up to `rows` groups per launch
+// (scratch of hankel_scratch_bytes(g, prec, rows) bytes, 256-byte aligned, and
+// dev_idx, device room for 2 * (number of grouped components) ints); one CTA
+// per group at the single-CTA sizes (scratch and dev_idx unused).
 void launch_hankel(const Geom& g, int prec, const df64* U, int64_t ldu, const df64* V, int64_t ldv,
                    const double* sigma, const int* grp_off_dev, const int* grp_idx_dev, const int* grp_off_host,
-                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, double oscale,
-                   cudaStream_t s);
+                   const int* grp_idx_host, int m, double* out, int64_t ldo, void* scratch, int rows, int* dev_idx,
+                   double oscale, cudaStream_t s);
+// bytes of Hankelization scratch for `rows` groups per launch (0 at the single-CTA sizes)
+size_t hankel_scratch_bytes(const Geom& g, int prec, int rows);
 
 }  // namespace ssa

@@ -105,10 +105,15 @@ def test_hankelize_matches_oracle(N, L, prec):
     sigma = np.abs(rng.standard_normal(r)) * 10 + 1
     U = rng.standard_normal((L, r)) / np.sqrt(L)
     V = rng.standard_normal((K, r)) / np.sqrt(K)
-    groups = [[0, 2], [1], [3, 4]]
+    # groups of two, one and no members: at the four-step sizes the components go in rounds
+    # (round r: the r-th member of every group) and an empty group reconstructs to zero
+    groups = [[0, 2], [1], [], [4, 3]]
     got = gpu_hankelize(N, L, sigma, U, V, groups, prec)
     tol = 1e-12 if prec == ssa.SSA_PREC_F64 else 2e-6
+    assert np.all(got[2] == 0.0)
     for g, idx in enumerate(groups):
+        if not idx:
+            continue
         if N <= 1000:
             ref = trajectory.diagonal_average((U[:, idx] * sigma[idx]) @ V[:, idx].T)
         else:
