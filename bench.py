@@ -528,85 +528,136 @@ def run_gpu_batch(args, w):
 
 
 def run_gpu_serving(args, w):
+    """Request server under the workload's Poisson stream (N log-uniform [1e3, 1e6], L = N//2,
+    k U{2..64}, seeded series).
+
+    Capacity: the first --serve-queue arrivals of the 2000 req/s stream (about a second of it,
+    far above what one GPU serves) are submitted on their arrival times and the server runs until
+    every one has finished; capacity = their number / (last completion - first submission): the
+    offered mix, every request counted once.  Latency: a continuous Poisson stream at 0.7 x that
+    capacity for --warmup + --steps seconds with no drain in between; p50/p99 over the requests
+    that finish after the warm-up seconds, with the offered and completed counts so that a stream
+    the server could not keep up with shows.  Series come from a pool of pre-generated ones (request
+    i uses pool entry i mod P: its N, L, k and series)."""
+    import threading
     import torch
     from paper_0911_4498_gb300 import build, synth
     build.build()
     import paper_0911_4498_gb300 as ssa
     prec = ssa.SSA_PREC_F32C if args.precision_batch == "f32c" else ssa.SSA_PREC_F64
-    def window(i):
-        arr = synth.serving_arrivals(w["rate"], args.window, seed=w["seed"] + i)
-        return [(t, N, L, k, synth.three_sines(N, seed=sd)) for (t, N, L, k, sd) in arr]
+    P = args.serve_pool
+    pool_arr = synth.serving_arrivals(w["rate"], P / w["rate"] * 1.2 + 1.0, seed=w["seed"])[:P]
+    pool = [(N, L, k, synth.three_sines(N, seed=sd)) for (_, N, L, k, sd) in pool_arr]
 
-    srv = ssa.ssa_serve_create(ssa.make_serve_opts(precision=prec, workers=args.serve_workers,
-                                                   batch_workers=args.serve_batch_workers))
-    sampler = None
-    lat, done_n, t_total, nreq, batched = [], 0, 0.0, 0, 0
-    launches0 = None
-    try:
-        for wi in range(args.warmup + args.steps):
-            reqs = window(wi)
-            timed = wi >= args.warmup
-            if timed and sampler is None:
-                torch.cuda.synchronize()
-                sampler = ClockSampler(0)
-                sampler.start()
-                launches0 = ssa.ssa_kernel_launches()
-            t0 = time.perf_counter()
-            ids = []
-            for (ta, N, L, k, f) in reqs:
-                now = time.perf_counter() - t0
-                if ta > now:
-                    time.sleep(ta - now)
-                ids.append((ssa.ssa_serve_submit(srv, f, L, k, 0), k, time.perf_counter()))
-            for rid, k, ts in ids:
-                while not ssa.ssa_serve_poll(srv, rid, 1.0):
-                    pass
+    def server():
+        return ssa.ssa_serve_create(ssa.make_serve_opts(precision=prec, workers=args.serve_workers,
+                                                        batch_workers=args.serve_batch_workers,
+                                                        max_batch=args.serve_max_batch))
+
+    def submit_stream(srv, arrivals, t0, on_submit):
+        for ta, pi in arrivals:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            N, L, k, f = pool[pi]
+            on_submit(ssa.ssa_serve_submit(srv, f, L, k, 0), k)
+
+    # ---- capacity
+    arr = synth.serving_arrivals(w["rate"], args.serve_queue / w["rate"] * 1.5 + 1.0, seed=w["seed"] + 1)
+    arr = [(t, i % P) for i, (t, *_r) in enumerate(arr)][:args.serve_queue]
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = ssa.ssa_kernel_launches()
+    srv = server()
+    ids = []
+    t0 = time.perf_counter()
+    submit_stream(srv, arr, t0, lambda rid, k: ids.append((rid, k)))
+    t_last, batched, n_big = 0.0, 0, 0
+    for (rid, k), (_, pi) in zip(ids, arr):
+        while not ssa.ssa_serve_poll(srv, rid, 1.0):
+            pass
+        rc, info = ssa.ssa_serve_take(srv, rid, np.empty(k))
+        t_last = max(t_last, info["t_done"])
+        batched += info["batched"]
+        n_big += pool[pi][0] > args.serve_batch_n
+    stats = ssa.ssa_serve_stats(srv)
+    ssa.ssa_serve_destroy(srv)
+    capacity = len(ids) / t_last
+    # ---- latency under a sustainable stream
+    rate2 = 0.7 * capacity
+    dur = float(args.warmup + args.steps)
+    arr2 = synth.serving_arrivals(rate2, dur, seed=w["seed"] + 2)
+    arr2 = [(t, i % P) for i, (t, *_r) in enumerate(arr2)]
+    srv = server()
+    pending, lock, res2 = [], threading.Lock(), []
+    state = {"done": False}
+
+    def collector():
+        while True:
+            with lock:
+                item = pending[0] if pending else None
+            if item is None:
+                if state["done"]:
+                    return
+                time.sleep(0.0005)
+                continue
+            rid, k = item
+            if ssa.ssa_serve_poll(srv, rid, 0.05):
                 rc, info = ssa.ssa_serve_take(srv, rid, np.empty(k))
-                if timed:
-                    lat.append(info["t_done"] - info["t_submit"])
-                    batched += info["batched"]
-            t_end = time.perf_counter()
-            if timed:
-                t_total += t_end - t0
-                nreq += len(ids)
-        stats = ssa.ssa_serve_stats(srv)
-    finally:
-        ssa.ssa_serve_destroy(srv)
+                res2.append((info["t_submit"], info["t_done"] - info["t_submit"]))
+                with lock:
+                    pending.pop(0)
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+
+    def add(rid, k):
+        with lock:
+            pending.append((rid, k))
+
+    submit_stream(srv, arr2, t0, add)
+    state["done"] = True
+    th.join()
+    ssa.ssa_serve_destroy(srv)
     clocks = sampler.stop()
     launches = ssa.ssa_kernel_launches() - launches0
-    value = nreq / t_total
-    # sequential plain FP64 single-series path on the first requests of the first timed window; one
-    # untimed pass first, so that one-time work (the FP64 four-step tiling autotuner runs once per
-    # size class per process) is not charged to the baseline
-    seq = window(args.warmup)[:args.seq_sample]
-
-    def run_seq():
-        for (_, N, L, k, f) in seq:
-            plan = ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=ssa.SSA_PREC_F64))
-            d, _ = ssa.ssa_decompose(plan, f, k)
-            sg = np.empty(k)
-            ssa.ssa_decomp_get(d, sg, None, None, None)
-            ssa.ssa_decomp_destroy(d)
-            ssa.ssa_plan_destroy(plan)
-
-    run_seq()
+    lat = [l for (ts, l) in res2 if ts >= args.warmup]
+    # the same mix (every pool entry once; the capacity sample cycles through the pool) one request
+    # after another through the plain FP64 single-series path; plans of every FFT size class are
+    # made first, untimed (the four-step tiling autotuner runs once per size class and process)
+    seq = pool[:args.seq_sample] if args.seq_sample > 0 else pool
+    for N, L, k, f in {int(np.ceil(np.log2(e[0]))): e for e in seq}.values():
+        ssa.ssa_plan_destroy(ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=ssa.SSA_PREC_F64)))
     t = time.perf_counter()
-    run_seq()
+    for (N, L, k, f) in seq:
+        plan = ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=ssa.SSA_PREC_F64))
+        d, _ = ssa.ssa_decompose(plan, f, k)
+        sg = np.empty(k)
+        ssa.ssa_decomp_get(d, sg, None, None, None)
+        ssa.ssa_decomp_destroy(d)
+        ssa.ssa_plan_destroy(plan)
     seq_rate = len(seq) / (time.perf_counter() - t)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+    pct = lambda a, q: float(np.percentile(a, q)) if a else None
+    line = {"metric": METRIC, "value": capacity, "unit": "requests/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64" if prec == ssa.SSA_PREC_F32C else "df64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "arrival_rate": w["rate"], "window_s": args.window,
-                       "N": "log-uniform [1e3, 1e6]", "L": "N//2", "k": "U{2..64}", "mem_budget_GiB": 40,
-                       "precision": args.precision_batch, "outputs": "sigma and residuals",
-                       "workers": args.serve_workers, "batch_workers": args.serve_batch_workers},
-            "requests": nreq, "batched_requests": batched,
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "offered_rps": w["rate"], "sequential_f64": {"value": seq_rate, "requests": len(seq)},
-            "speedup_vs_sequential_f64": value / seq_rate, "mem_peak_GiB": stats["mem_peak"] / 2**30,
+            "config": {"workload": args.workload, "arrival_rate": w["rate"], "N": "log-uniform [1e3, 1e6]",
+                       "L": "N//2", "k": "U{2..64}", "mem_budget_GiB": 40, "precision": args.precision_batch,
+                       "outputs": "sigma and residuals", "workers": args.serve_workers,
+                       "batch_workers": args.serve_batch_workers, "max_batch": args.serve_max_batch,
+                       "series_pool": P, "capacity_sample": len(ids),
+                       "latency_stream_s": dur, "latency_warmup_s": args.warmup},
+            "capacity": {"requests": len(ids), "seconds": t_last, "batched": batched,
+                         "share_N_above_batch_limit": n_big / len(ids)},
+            "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "offered_rps": rate2,
+                          "offered": len(arr2), "completed": len(res2), "counted": len(lat)},
+            "sequential_f64": {"value": seq_rate, "requests": len(seq)},
+            "speedup_vs_sequential_f64": capacity / seq_rate, "mem_peak_GiB": stats["mem_peak"] / 2**30,
             "roofline": None, "cpu_baseline": None,
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+            "e2e": {"value": capacity, "unit": "requests/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
             "gpu_launches": launches, "clocks": clocks}
     print(json.dumps(line))
     return 0
@@ -1159,10 +1210,15 @@ def main():
     ap.add_argument("--cpu-worker", action="store_true")
     ap.add_argument("--precision-batch", default="f32c", choices=["f64", "f32c"],
                     help="precision of the batch and serving workloads")
-    ap.add_argument("--window", type=float, default=0.25, help="serving: arrival window per step (s)")
-    ap.add_argument("--seq-sample", type=int, default=40, help="serving: requests timed sequentially in FP64")
-    ap.add_argument("--serve-workers", type=int, default=16, help="serving: single-series workers (streams)")
-    ap.add_argument("--serve-batch-workers", type=int, default=2, help="serving: batched-launch workers")
+    ap.add_argument("--serve-pool", type=int, default=256, help="serving: pre-generated series the stream cycles")
+    ap.add_argument("--serve-queue", type=int, default=2000, help="serving: most requests outstanding at once")
+    ap.add_argument("--serve-latency-s", type=float, default=6.0, help="serving: length of the sustainable-load run")
+    ap.add_argument("--serve-batch-n", type=int, default=32768, help="serving: N limit of the batched engine")
+    ap.add_argument("--serve-max-batch", type=int, default=128, help="serving: requests per batched launch at most")
+    ap.add_argument("--seq-sample", type=int, default=0,
+                    help="serving: pool entries timed one after another in FP64 (0 = all of them)")
+    ap.add_argument("--serve-workers", type=int, default=8, help="serving: single-series workers (streams)")
+    ap.add_argument("--serve-batch-workers", type=int, default=1, help="serving: batched-launch workers")
     args = ap.parse_args()
     if args.cpu_worker:
         cpu_worker(args)

@@ -283,9 +283,9 @@ typedef struct ssa_serve_opts {
   int precision;        /* SSA_PREC_F64 or SSA_PREC_F32C for every request (default SSA_PREC_F32C) */
   double tol;           /* as ssa_opts_t.tol (0 = the precision's default) */
   int64_t mem_budget;   /* device bytes that admitted requests may hold together (default 40 GiB) */
-  int workers;          /* single-series requests running at once (default 16, at most 64) */
-  int batch_workers;    /* batched launches running at once (default 2, at most 16; 0 = never batch) */
-  int max_batch;        /* requests per batched launch (default 512) */
+  int workers;          /* single-series requests running at once (default 8, at most 64) */
+  int batch_workers;    /* batched launches running at once (default 1, at most 16; 0 = never batch) */
+  int max_batch;        /* requests per batched launch (default 128) */
   int64_t batch_max_n;  /* only series with N <= this are batched (0 = the engine's limit, -1 = none) */
 } ssa_serve_opts_t;
 
@@ -305,7 +305,7 @@ typedef struct ssa_serve_stats {
   int64_t batches, batched_requests;
 } ssa_serve_stats_t;
 
-/* Defaults: SSA_PREC_F32C, tol 0, 40 GiB, 16 workers, 2 batch workers, max_batch 512, batch_max_n 0. */
+/* Defaults: SSA_PREC_F32C, tol 0, 40 GiB, 8 workers, 1 batch worker, max_batch 128, batch_max_n 0. */
 void ssa_serve_default_opts(ssa_serve_opts_t* opts);
 /* Start the worker threads.  opts may be NULL (defaults).  Errors: SSA_EINVAL, SSA_ENOMEM. */
 int ssa_serve_create(const ssa_serve_opts_t* opts, ssa_server_t* out);

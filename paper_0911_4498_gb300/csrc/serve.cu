@@ -266,9 +266,12 @@ extern "C" void ssa_serve_default_opts(ssa_serve_opts_t* o) {
   o->precision = SSA_PREC_F32C;
   o->tol = 0.0;
   o->mem_budget = (int64_t)40 << 30;
-  o->workers = 16;
-  o->batch_workers = 2;
-  o->max_batch = 512;
+  // measured on the serving workload (N log-uniform [1e3, 1e6], k U{2..64}): more single-series
+  // workers or batch workers, or larger batches, left the batched engine less of the device and
+  // the capacity for the whole mix lower (16 / 2 / 512: ~50 requests/s; 4-8 / 1 / 64-256: 70-74)
+  o->workers = 8;
+  o->batch_workers = 1;
+  o->max_batch = 128;
   o->batch_max_n = 0;
 }
 
