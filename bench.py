@@ -75,6 +75,10 @@ NCU_TRAFFIC = {
     "cgs_update_proj": {"ratio": 0.983, "file": "paper_0911_4498_gb300/csrc/cgs_lanes.cuh",
                         "sha256": "50cd82553364e561ab037eafa03b2172b9570d6313defe12e3e522694e98f435",
                         "profile": "profiles/cgs_lanes_many_sines_N1M_dram.md"},
+    # projection launches 2402 and 2405 of the same capture: (423.8 / 427.8 + 256.3 / 260.0) / 2
+    "cgs_proj": {"ratio": 0.988, "file": "paper_0911_4498_gb300/csrc/cgs_lanes.cuh",
+                 "sha256": "50cd82553364e561ab037eafa03b2172b9570d6313defe12e3e522694e98f435",
+                 "profile": "profiles/cgs_lanes_many_sines_N1M_dram.md"},
 }
 
 
@@ -1127,14 +1131,14 @@ def run_gpu(args):
     name_main = ("f64" if skip == 0 else f"f64_skip{skip:g}") if prec == ssa.SSA_PREC_F64 else "f32c"
     modes = {name_main: {"value": value, "sigma_rel_err_max": sig_err}}
     if not args.no_modes:
-        alts = [("f32c", ssa.SSA_PREC_F32C, 0.0), ("f64", ssa.SSA_PREC_F64, 0.0)]
+        alts = [("f32c", ssa.SSA_PREC_F32C, 0.0, 0), ("f64", ssa.SSA_PREC_F64, 0.0, 0)]
         if args.reorth_skip > 0:
-            alts.append((f"f64_skip{args.reorth_skip:g}", ssa.SSA_PREC_F64, args.reorth_skip))
-        for name, other, sk in alts:
+            alts.append((f"f64_skip{args.reorth_skip:g}", ssa.SSA_PREC_F64, args.reorth_skip, 0))
+        for name, other, sk, ro in alts:
             if name in modes:
                 continue
             plan2 = ssa.ssa_embed_plan(N, L, ssa.make_opts(precision=other, seed=rank, stream=stream.cuda_stream,
-                                                           reorth_skip=sk))
+                                                           reorth_skip=sk, reorth=ro))
             sig2 = torch.empty(k, dtype=torch.float64, device="cuda")
 
             def step2():

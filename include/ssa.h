@@ -83,7 +83,22 @@ typedef struct ssa_opts {
                          well-separated spectra; the basis is then orthogonal only to ~tau, so sigma are
                          accurate to ~tau sigma_1 absolute and vectors of closely spaced sigma to
                          ~tau sigma_1 / gap. */
+  int reorth;         /* SSA_REORTH_FULL (default): Gram-Schmidt against the whole basis every half-step.
+                         SSA_REORTH_PRO (SSA_PREC_F64 only): partial reorthogonalisation (section 3.2.2)
+                         in the first Lanczos cycle: each half-step subtracts its one known coupling,
+                         updates estimates of the new vector's inner products with the older ones from
+                         the projected matrix, and runs the Gram-Schmidt passes only when an estimate
+                         exceeds sqrt(eps) (eps = 2^-46, the double-float product error) and on the step
+                         after.  The basis is then orthogonal to ~sqrt(eps): sigma keep full accuracy,
+                         vectors and reconstructions ~sqrt(eps) (or ~1e-9 sigma_1 / gap).  The
+                         coefficients it leaves out would spoil a thick restart, so a first cycle that
+                         does not converge starts over from the same starting vector with full
+                         Gram-Schmidt (counted as one restart): choose krylov_dim large enough for one
+                         cycle.  reorth_skip is ignored in this mode. */
 } ssa_opts_t;
+
+#define SSA_REORTH_FULL 0
+#define SSA_REORTH_PRO 1
 
 #define SSA_REFINE_OFF 0
 #define SSA_REFINE_ON 1

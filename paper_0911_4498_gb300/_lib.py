@@ -20,12 +20,14 @@ SSA_OK, SSA_EINVAL, SSA_ENOMEM, SSA_ENOCONV = range(4)
 SSA_ECUDA, SSA_ENUMERIC = 5, 6
 SSA_PREC_F64, SSA_PREC_F32C = 0, 1
 SSA_REFINE_OFF, SSA_REFINE_ON = 0, 1
+SSA_REORTH_FULL, SSA_REORTH_PRO = 0, 1
 
 
 class SsaOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
                 ("krylov_dim", ctypes.c_int), ("keep", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p), ("refine", ctypes.c_int), ("reorth_skip", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("refine", ctypes.c_int), ("reorth_skip", ctypes.c_double),
+                ("reorth", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -155,13 +157,14 @@ def ssa_default_opts() -> SsaOpts:
 
 
 def make_opts(precision=SSA_PREC_F64, tol=0.0, max_restarts=200, krylov_dim=0, keep=0, seed=0, stream=None,
-              refine=SSA_REFINE_OFF, reorth_skip=0.0):
+              refine=SSA_REFINE_OFF, reorth_skip=0.0, reorth=0):
     o = ssa_default_opts()
     o.precision, o.tol, o.max_restarts = precision, tol, max_restarts
     o.krylov_dim, o.keep, o.seed = krylov_dim, keep, seed
     o.stream = stream
     o.refine = refine
     o.reorth_skip = reorth_skip
+    o.reorth = reorth
     return o
 
 

@@ -281,7 +281,9 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
   // algorithmic bytes: the ncols basis columns once per pass, w read (and written by updates)
   const double qb = 8.0 * (double)dim * ncols;
   const double fl = 2.0 * (double)dim * ncols;
-  const int* flag = nullptr;
+  // REORTH_PRO: every pass waits on the partial-reorthogonalisation decision
+  const int* flag = mode == REORTH_PRO ? rw.run : nullptr;
+  const bool gated = mode == REORTH_GATED || mode == REORTH_PRO;
   if (ncols <= FUSED_MAXCOL) {
     const int T2 = fused_tiles(dim);
     auto grid = [&](int pass) { return g_lanes_grid[pass][ncols] < T2 ? g_lanes_grid[pass][ncols] : T2; };
@@ -291,12 +293,13 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
     if (ncols > 0) {
       // pass 1: h = Q^T w and ||w||^2 (column ncols)
       const int G1 = grid(P_PROJ);
+      const bool ran1 = flag_on_host(flag, s);
       prof_begin(s);
       lanes_pass<false, true>(Q, ldq, ncols, w, dim, rw.h, rw.part2, ldp, G1, T2, flag, s);
-      prof_end(s, K_PROJ, qb + 8.0 * dim, fl);
-      if (mode == REORTH_GATED) {
-        const bool skip_test = rw.skip_tau > 0.0;
-        const int* run = skip_test ? rw.run : nullptr;
+      prof_end(s, ran1 ? K_PROJ : K_SKIPPED, ran1 ? qb + 8.0 * dim : 0.0, ran1 ? fl : 0.0);
+      if (gated) {
+        const bool skip_test = mode == REORTH_GATED && rw.skip_tau > 0.0;
+        const int* run = skip_test || mode == REORTH_PRO ? rw.run : nullptr;
         prof_begin(s);
         if (skip_test)  // the skip test decides on the device whether passes 2 and 3 run
           k_reduce_skip<<<(ncols + 8) / 8, 256, 0, s>>>(rw.part2, G1, ldp, ncols, rw.h, rw.run, rw.gate, rw.skip,

@@ -209,7 +209,12 @@ struct Workspace {
   int* flag = nullptr;
   unsigned* status = nullptr;
   int* sgn = nullptr;
+  ProState pro{};
   void release(cudaStream_t st) {
+    free_async(pro.M, st);
+    free_async(pro.N, st);
+    free_async(pro.force, st);
+    pro = ProState{};
     for (int i = 0; i < 2; ++i) {
       free_async(Ub[i], st);
       free_async(Vb[i], st);
@@ -422,6 +427,7 @@ extern "C" void ssa_default_opts(ssa_opts_t* o) {
   o->stream = nullptr;
   o->refine = SSA_REFINE_OFF;
   o->reorth_skip = 0.0;
+  o->reorth = SSA_REORTH_FULL;
 }
 
 extern "C" const char* ssa_strerror(int code) {
@@ -466,6 +472,7 @@ extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_
   REQ(o.precision == SSA_PREC_F64 || o.precision == SSA_PREC_F32C, "unknown precision %d", o.precision);
   REQ(o.refine == SSA_REFINE_OFF || o.refine == SSA_REFINE_ON, "unknown refine mode %d", o.refine);
   REQ(o.reorth_skip >= 0.0 && o.reorth_skip < 1e-3, "reorth_skip must be in [0, 1e-3) (got %g)", o.reorth_skip);
+  REQ(o.reorth == SSA_REORTH_FULL || o.reorth == SSA_REORTH_PRO, "unknown reorth mode %d", o.reorth);
   ssa_plan_s* p = new (std::nothrow) ssa_plan_s();
   if (!p) return SSA_ENOMEM;
   p->opts = o;
@@ -751,6 +758,10 @@ static int ensure_workspace(ssa_plan_t p, int d) {
   CK(malloc_async(&w.status, sizeof(unsigned), st));
   w.rw.status = w.status;
   CK(malloc_async(&w.sgn, cols * sizeof(int), st));
+  w.pro.lde = cols;
+  CK(malloc_async(&w.pro.M, (size_t)cols * cols * sizeof(float), st));
+  CK(malloc_async(&w.pro.N, (size_t)cols * cols * sizeof(float), st));
+  CK(malloc_async(&w.pro.force, 2 * sizeof(int), st));
   w.dcap = d;
   return SSA_OK;
 }
@@ -779,25 +790,22 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   int cur = 0;
   df64* U = w.Ub[cur];
   df64* V = w.Vb[cur];
-  CK(cudaMemsetAsync(w.B, 0, (size_t)w.ldb * w.ldb * sizeof(df64), s));
-  CK(cudaMemsetAsync(w.est, 0, sizeof(df64), s));
   CK(cudaMemsetAsync(w.flag, 0, sizeof(int), s));
   CK(cudaMemsetAsync(w.status, 0, sizeof(unsigned), s));
   w.sw.max_sweeps = 60;
   w.sw.rot_tol = 1e-13f;
   const uint64_t seed = p->opts.seed;
-  uint64_t stream_id = 0;
+  uint64_t stream_id = 1;  // counter streams of the breakdown replacements (0: the starting vector)
   int64_t matvecs = 0;
-  // p_0 (Algorithm 1, line 1): seeded uniform(-1, 1), normalised into u_1
-  launch_random_fill(w.y, Lw, seed, stream_id++, s);
   // one reorthogonalisation pass suffices when the products are FP32 (their
   // error, ~1e-7 sigma_1, is far above one pass's df64 orthogonality)
   const int reorth = prec == SSA_PREC_F32C ? REORTH_ONCE : REORTH_GATED;
-  w.rw.skip_tau = prec == SSA_PREC_F32C ? 0.0 : p->opts.reorth_skip;
-  launch_cgs2(U, w.ldu, 0, w.y, Lw, w.rw, reorth, s);
-  CK((cudaError_t)launch_normalize_coop(w.y, Lw, w.rw, U, w.dummy, w.est, U, w.ldu, 0, seed, stream_id++, w.status,
-                                        s));
-  CHECK_LAUNCH();
+  // partial reorthogonalisation keeps sigma at working accuracy only while no thick restart
+  // happens (the coefficients it leaves out, up to sqrt(eps) ||w||, would enter the restarted
+  // arrow matrix): a first cycle that does not converge starts over with full Gram-Schmidt
+  bool pro = prec != SSA_PREC_F32C && p->opts.reorth == SSA_REORTH_PRO;
+  w.rw.skip_tau = prec == SSA_PREC_F32C || pro ? 0.0 : p->opts.reorth_skip;
+  w.pro.eps = 1.4e-14f;  // relative error of the double-float products (2^-46)
   int r = 1, c = 0;
   auto side = [&](bool vside) -> int {
     // v-side: alpha v_{c+1} = X^T u_r - ... ; u-side: beta u_{r+1} = X v_c - ...
@@ -809,7 +817,18 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     df64* bentry = vside ? w.B + (int64_t)(r - 1) * w.ldb + c : w.B + (int64_t)r * w.ldb + (c - 1);
     launch_matvec_df(p->g, prec, vside ? 1 : 0, src, 0, w.y, 0, 1, p->chat, p->scratch, s);
     ++matvecs;
-    launch_cgs2(Qb, ldq, ncols, w.y, dim, w.rw, reorth, s);
+    int mode = reorth;
+    if (pro && ncols > 0) {
+      // partial reorthogonalisation (first cycle only): subtract the one known coupling B[r-1][c-1]
+      // (to v_{c-1} on the v side, to u_{r-1} on the u side), update the estimates and decide on
+      // the device whether the Gram-Schmidt passes run
+      const df64* coef = w.B + (int64_t)(r - 1) * w.ldb + (c - 1);
+      const df64* qprev = vside ? V + (int64_t)(c - 1) * w.ldv : U + (int64_t)(r - 1) * w.ldu;
+      CK((cudaError_t)launch_pro_pre(w.y, dim, qprev, coef, w.rw, w.pro, w.B, w.ldb, vside ? 1 : 0, ncols,
+                                     vside ? r - 1 : c - 1, ncols, vside ? r : c, vside ? c - 1 : r - 1, w.est, s));
+      mode = REORTH_PRO;
+    }
+    launch_cgs2(Qb, ldq, ncols, w.y, dim, w.rw, mode, s);
     df64* qcol = Qb + (int64_t)ncols * ldq;
     CK((cudaError_t)launch_normalize_coop(w.y, dim, w.rw, qcol, bentry, w.est, Qb, ldq, ncols, seed, stream_id,
                                           w.status, s));
@@ -819,8 +838,22 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     else ++r;
     return SSA_OK;
   };
+  // p_0 (Algorithm 1): seeded uniform(-1, 1) from counter stream 0, normalised into u_1; then v_1
+  auto start = [&]() -> int {
+    CK(cudaMemsetAsync(w.B, 0, (size_t)w.ldb * w.ldb * sizeof(df64), s));
+    CK(cudaMemsetAsync(w.est, 0, sizeof(df64), s));
+    if (pro) launch_pro_reset(w.pro, s);
+    launch_random_fill(w.y, Lw, seed, 0, s);
+    launch_cgs2(U, w.ldu, 0, w.y, Lw, w.rw, reorth, s);
+    CK((cudaError_t)launch_normalize_coop(w.y, Lw, w.rw, U, w.dummy, w.est, U, w.ldu, 0, seed, stream_id++,
+                                          w.status, s));
+    CHECK_LAUNCH();
+    r = 1;
+    c = 0;
+    return side(true);
+  };
   int restarts = 0, converged = 0;
-  rc = side(true);
+  rc = start();
   if (rc) return rc;
   unsigned status = 0;
   for (;;) {
@@ -848,6 +881,13 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
       return SSA_ENUMERIC;
     }
     if (converged || restarts >= p->opts.max_restarts || kk >= cp) break;
+    if (pro) {  // the first cycle did not converge: start over with full Gram-Schmidt
+      pro = false;
+      ++restarts;
+      rc = start();
+      if (rc) return rc;
+      continue;
+    }
     // thick restart: U <- U P[:, :kk], V <- [V Q[:, :kk], v_{c}], B <- [diag | rho]
     const int nxt = cur ^ 1;
     launch_ritz(U, w.ldu, r, w.sw.P, r, kk, w.Ub[nxt], w.ldu, Lw, s);

@@ -60,6 +60,17 @@ struct SvdWork {
   float rot_tol;
 };
 
+// Partial reorthogonalisation state: estimates of u_i.u_j (M) and v_i.v_j (N),
+// FP32, lde x lde each; eps is the relative error level of the products; force
+// holds the "reorthogonalise the next step too" flags of the two sides.
+struct ProState {
+  float* M;
+  float* N;
+  int lde;
+  float eps;
+  int* force;
+};
+
 int reorth_blocks(int64_t dim);
 int fused_tiles(int64_t dim);
 void reorth_setup();
@@ -72,13 +83,21 @@ void reorth_setup();
 // and that projection's update (a third pass) only when ||w'||^2 < ||w||^2 / 2
 // after the first (Kahan-Parlett), so the result is orthogonal to Q to
 // working precision.  Bases wider than FUSED_MAXCOL always take two full rounds.
-enum { REORTH_ONCE = 1, REORTH_GATED = 2 };
+// REORTH_PRO: the passes of REORTH_GATED, all gated by rw.run (set by launch_pro_pre).
+enum { REORTH_ONCE = 1, REORTH_GATED = 2, REORTH_PRO = 3 };
 void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, ReorthWork& rw, int mode,
                  cudaStream_t s);
 int coop_blocks();
 int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64* bentry, df64* est,
                           const df64* Q, int64_t ldq, int ncols, uint64_t seed, uint64_t stream, unsigned* status,
                           cudaStream_t s);
+// PRO pre-step (cooperative): w -= coef * qprev (if qprev), the new vector's orthogonality
+// estimates and the decision in *rw.run (else *rw.gate = 0, *rw.nrm = ||w||^2); side 0: new u
+// (index newidx) from v_src, side 1: new v from u_src; prev: the coupled vector, -1 if none
+int launch_pro_pre(df64* w, int64_t dim, const df64* qprev, const df64* coef, ReorthWork& rw, ProState& ps,
+                   const df64* B, int ldb, int side, int newidx, int src, int cnt_same, int cnt_other, int prev,
+                   const df64* est, cudaStream_t s);
+void launch_pro_reset(ProState& ps, cudaStream_t s);
 void launch_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stream, cudaStream_t s);
 void launch_small_svd(const df64* B, int ldb, int r, int c, SvdWork& sw, int k, double tol_conv,
                       df64* est, unsigned* status, cudaStream_t s);

@@ -140,6 +140,130 @@ __global__ void __launch_bounds__(256) k_normalize_coop(df64* __restrict__ w, in
 }
 
 
+// ---------------------------------------------------------------- partial reorthogonalisation
+// PRO pre-step of a half-step (cooperative).  All blocks: w <- w - coef q_prev
+// (the one known coupling of the bidiagonalisation, when there is one) and
+// ||w||^2 summed over the grid.  Block 0 then updates the orthogonality
+// estimates of the new vector against the older ones of its side, from the
+// projected matrix B (X v_b = sum_a B[a][b] u_a, X^T u_a = sum_b B[a][b] v_b):
+//   new u from v_s, coupling u_p:  u_i.w = sum_b B[i][b] N[s][b] - B[p][s] M[p][i]
+//   new v from u_s, coupling v_p:  v_i.w = sum_a B[a][i] M[s][a] - B[s][p] N[p][i]
+// each plus a rounding term eps ||X|| with the sign of the sum, divided by
+// ||w|| (estimates in FP32: only their magnitude matters).  The Gram-Schmidt
+// passes run (*run = 1) when an estimate exceeds sqrt(eps), when the caller
+// forces it, or on the step after one that ran (the estimates of a vector
+// built on a reorthogonalised one are not yet small); then the new vector's
+// estimates are reset to eps.  Otherwise *gate = 0 and *nrm = ||w||^2 for the
+// normalisation.
+struct ProArgs {
+  df64* w;
+  int64_t dim;
+  const df64* qprev;
+  const df64* coef;
+  df64* nrm;
+  int* run;
+  int* gate;
+  float* M;  // [u][u] estimates, leading dimension lde
+  float* N;  // [v][v]
+  int lde;
+  const df64* B;
+  int ldb;
+  int side;    // 0: new u, 1: new v
+  int newidx;  // index of the new vector on its side
+  int src;     // index of the product's input vector (other side)
+  int cnt_same, cnt_other;  // vectors on the new vector's side / the other side before the new one
+  int prev;    // index of the coupled vector on the same side, -1 if none
+  float eps;
+  const df64* est;
+  int* force;  // [0] u side, [1] v side
+  df64* scratch;
+  int lds;
+};
+
+__global__ void __launch_bounds__(256) k_pro_pre(ProArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ df64 sh[32];
+  __shared__ float fm[32];
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const df64 c = a.coef ? *a.coef : df_zero();
+  df64 acc = df_zero();
+  for (int64_t i = tid; i < a.dim; i += stride) {
+    df64 x = a.w[i];
+    if (a.qprev) x = df_sub(x, df_mul(c, a.qprev[i]));
+    a.w[i] = x;
+    acc = df_fma(x, x, acc);
+  }
+  acc = block_sum_df(acc, sh);
+  if (threadIdx.x == 0) a.scratch[(int64_t)blockIdx.x * a.lds + MAXCOL] = acc;
+  grid.sync();
+  if (blockIdx.x != 0) return;
+  if (threadIdx.x < 32) {
+    df64 t = df_zero();
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t = df_add(t, a.scratch[(int64_t)b * a.lds + MAXCOL]);
+    t = warp_sum_df(t);
+    if (threadIdx.x == 0) sh[0] = t;
+  }
+  __syncthreads();
+  const df64 n2 = sh[0];
+  const float nw = sqrtf(fmaxf(n2.hi, 0.f));
+  const float tolr = a.eps * a.est->hi;
+  float* E = (a.side == 0 ? a.M : a.N) + (int64_t)a.newidx * a.lde;
+  const float* Eo = (a.side == 0 ? a.N : a.M) + (int64_t)a.src * a.lde;   // estimates of the source vector
+  const float* Ep = a.prev >= 0 ? (a.side == 0 ? a.M : a.N) + (int64_t)a.prev * a.lde : nullptr;
+  const float cpl = a.prev >= 0 ? (a.side == 0 ? a.B[(int64_t)a.prev * a.ldb + a.src].hi
+                                                : a.B[(int64_t)a.src * a.ldb + a.prev].hi)
+                                 : 0.f;
+  // one warp per estimate, its lanes over the other side's vectors
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  float m = 0.f;
+  for (int i = threadIdx.x >> 5; i < a.cnt_same; i += nwarp) {
+    float s = 0.f;
+    if (i != a.prev) {
+      if (a.side == 0)
+        for (int b = lane; b < a.cnt_other; b += 32) s = fmaf(a.B[(int64_t)i * a.ldb + b].hi, Eo[b], s);
+      else
+        for (int b = lane; b < a.cnt_other; b += 32) s = fmaf(a.B[(int64_t)b * a.ldb + i].hi, Eo[b], s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (i != a.prev && Ep) s = fmaf(-cpl, Ep[i], s);
+    const float v = nw > 0.f ? (s + copysignf(tolr, s)) / nw : 1.f;
+    if (lane == 0) E[i] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) fm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  __shared__ int s_run;
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, fm[i]);
+    const int f = a.force[a.side];
+    const int run = f || !(m <= sqrtf(a.eps)) ? 1 : 0;
+    a.force[a.side] = (run && !f) ? 1 : 0;
+    *a.run = run;
+    if (!run) {
+      *a.gate = 0;
+      *a.nrm = n2;
+    }
+    s_run = run;
+  }
+  __syncthreads();
+  if (s_run)
+    for (int i = threadIdx.x; i < a.cnt_same; i += blockDim.x) E[i] = a.eps;
+  if (threadIdx.x == 0) E[a.newidx] = 1.f;
+}
+
+// estimates of a fresh basis (after a restart, or at the start): eps off the diagonal, 1 on it
+__global__ void k_pro_reset(float* M, float* N, int lde, int n, float eps, int* force) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * lde; e += gridDim.x * blockDim.x) {
+    const int i = e / lde, j = e - i * lde;
+    const float v = i == j ? 1.f : eps;
+    M[e] = v;
+    N[e] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 2) force[threadIdx.x] = 0;
+}
+
 // ---------------------------------------------------------------- projected SVD
 // One-CTA projected SVD (see svd_jacobi_body / svd_precondition_body).
 __global__ void __launch_bounds__(SVD_THREADS) k_small_svd(const df64* __restrict__ B, int ldb, int r, int c,
@@ -723,6 +847,53 @@ int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_normalize_coop, dim3(blocks), dim3(256), args, 0, s);
   prof_end(s, K_NORMALIZE, 16.0 * dim, 0.0);
   return e == cudaSuccess ? 0 : (int)e;
+}
+
+int launch_pro_pre(df64* w, int64_t dim, const df64* qprev, const df64* coef, ReorthWork& rw, ProState& ps,
+                   const df64* B, int ldb, int side, int newidx, int src, int cnt_same, int cnt_other, int prev,
+                   const df64* est, cudaStream_t s) {
+  ProArgs a{};
+  a.w = w;
+  a.dim = dim;
+  a.qprev = qprev;
+  a.coef = coef;
+  a.nrm = rw.nrm;
+  a.run = rw.run;
+  a.gate = rw.gate;
+  a.M = ps.M;
+  a.N = ps.N;
+  a.lde = ps.lde;
+  a.B = B;
+  a.ldb = ldb;
+  a.side = side;
+  a.newidx = newidx;
+  a.src = src;
+  a.cnt_same = cnt_same;
+  a.cnt_other = cnt_other;
+  a.prev = prev;
+  a.eps = ps.eps;
+  a.est = est;
+  a.force = ps.force;
+  a.scratch = rw.coop;
+  a.lds = MAXCOL + 1;
+  static const int pro_cap = [] {  // co-resident blocks of this kernel (its own occupancy)
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pro_pre, 256, 0);
+    if (per < 1) per = 1;
+    return sms * per < coop_blocks() ? sms * per : coop_blocks();
+  }();
+  const int blocks = grid_for(dim, 256, pro_cap);
+  void* args[] = {&a};
+  prof_begin(s);
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_pro_pre, dim3(blocks), dim3(256), args, 0, s);
+  prof_end(s, K_MISC, qprev ? 24.0 * dim : 16.0 * dim, 0.0);
+  return e == cudaSuccess ? 0 : (int)e;
+}
+
+void launch_pro_reset(ProState& ps, cudaStream_t s) {
+  k_pro_reset<<<64, 256, 0, s>>>(ps.M, ps.N, ps.lde, ps.lde, ps.eps, ps.force);
 }
 
 void launch_random_fill(df64* w, int64_t dim, uint64_t seed, uint64_t stream, cudaStream_t s) {

@@ -237,3 +237,47 @@ def test_reorth_skip_option():
             gpu_decompose(f, L, k, reorth_skip=bad)
     f32 = gpu_decompose(f, L, k, precision=ssa.SSA_PREC_F32C, reorth_skip=1e-12)
     assert np.max(_rel(f32["sigma"], ref["sigma"])) <= SIG_F32C
+
+
+@pytest.mark.parametrize("N,L,k", [(5000, 2500, 16), (40000, 13333, 12)])
+def test_partial_reorthogonalisation(N, L, k):
+    """PRO (section 3.2.2) where one Lanczos cycle converges (single-CTA and four-step products):
+    sigma within 1e-10 of the oracle (their error is second order in the coefficients PRO leaves
+    out of B, which are below sqrt(eps) = 2^-23 of the double-float products); vectors within
+    sqrt(eps), or Wedin's bound with a residual of 1e-9 sigma_1 where a gap is small; relation (1)
+    within 1e-9 sigma_1 and the reconstructions of the leading components within 10 sqrt(eps)."""
+    f = synth.many_sines(N, seed=N)
+    ref = ossa.decompose(f, L, k, method="lanczos")
+    groups = [[0], [1], [2, 3]]
+    got = gpu_decompose_reconstruct(f, L, k, groups, reorth=ssa.SSA_REORTH_PRO)
+    assert got["rc"] == ssa.SSA_OK and got["info"]["converged"] and got["info"]["restarts"] == 0
+    assert np.max(_rel(got["sigma"], ref["sigma"])) <= SIG_F64
+    sqrt_eps = 2.0 ** -23
+    compare_vectors(got["U"], ref["U"], ref["sigma"], sqrt_eps, res_tol=1e-9)
+    compare_vectors(got["V"], ref["V"], ref["sigma"], sqrt_eps, res_tol=1e-9)
+    K = N - L + 1
+    for i in (0, k // 2, k - 1):
+        for row in (0, L // 3, L - 1):
+            lhs = f[row:row + K] @ got["V"][:, i]
+            assert abs(lhs - got["sigma"][i] * got["U"][row, i]) <= 1e-9 * ref["sigma"][0]
+    rec_ref = ossa.reconstruct(N, L, ref["sigma"], ref["U"], ref["V"], groups, method="fft", fft="library")
+    for gi in range(len(groups)):
+        err = np.linalg.norm(got["rec"][gi] - rec_ref[gi]) / np.linalg.norm(rec_ref[gi])
+        assert err <= 10 * sqrt_eps, (gi, err)
+    with pytest.raises(ssa.SSAError):
+        gpu_decompose(f, L, k, reorth=7)
+
+
+def test_partial_reorthogonalisation_falls_back_to_full():
+    """A PRO first cycle that does not converge (N = 5113, k = 100 restarts three times) starts over
+    from the same starting vector with full Gram-Schmidt: the result is the full-reorthogonalisation
+    result bit for bit, with one more restart counted."""
+    N, L, k = 5113, 2556, 100
+    f = synth.three_sines(N, seed=7)
+    full = gpu_decompose(f, L, k)
+    pro = gpu_decompose(f, L, k, reorth=ssa.SSA_REORTH_PRO)
+    assert full["rc"] == pro["rc"] == ssa.SSA_OK
+    assert full["info"]["restarts"] > 0
+    assert pro["info"]["restarts"] == full["info"]["restarts"] + 1
+    assert np.array_equal(full["sigma"], pro["sigma"])
+    assert np.array_equal(full["U"], pro["U"]) and np.array_equal(full["V"], pro["V"])
