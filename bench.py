@@ -556,7 +556,8 @@ def run_gpu_serving(args, w):
     def server():
         return ssa.ssa_serve_create(ssa.make_serve_opts(precision=prec, workers=args.serve_workers,
                                                         batch_workers=args.serve_batch_workers,
-                                                        max_batch=args.serve_max_batch))
+                                                        max_batch=args.serve_max_batch,
+                                                        grid_cap=args.serve_grid_cap))
 
     def submit_stream(srv, arrivals, t0, on_submit):
         for ta, pi in arrivals:
@@ -652,6 +653,7 @@ def run_gpu_serving(args, w):
                        "L": "N//2", "k": "U{2..64}", "mem_budget_GiB": 40, "precision": args.precision_batch,
                        "outputs": "sigma and residuals", "workers": args.serve_workers,
                        "batch_workers": args.serve_batch_workers, "max_batch": args.serve_max_batch,
+                       "grid_cap": args.serve_grid_cap,
                        "series_pool": P, "capacity_sample": len(ids),
                        "latency_stream_s": dur, "latency_warmup_s": args.warmup},
             "capacity": {"requests": len(ids), "seconds": t_last, "batched": batched,
@@ -1230,6 +1232,8 @@ def main():
     ap.add_argument("--seq-sample", type=int, default=0,
                     help="serving: pool entries timed one after another in FP64 (0 = all of them)")
     ap.add_argument("--serve-workers", type=int, default=8, help="serving: single-series workers (streams)")
+    ap.add_argument("--serve-grid-cap", type=int, default=0,
+                    help="serving: CTAs per persistent kernel of a request (0 = the whole device)")
     ap.add_argument("--serve-batch-workers", type=int, default=1, help="serving: batched-launch workers")
     args = ap.parse_args()
     if args.cpu_worker:

@@ -95,6 +95,11 @@ typedef struct ssa_opts {
                          does not converge starts over from the same starting vector with full
                          Gram-Schmidt (counted as one restart): choose krylov_dim large enough for one
                          cycle.  reorth_skip is ignored in this mode. */
+  int grid_cap;       /* most CTAs of one launch of the persistent reorthogonalisation passes and the
+                         cooperative normalisation (0, default: as many as are resident on the whole
+                         device).  A caller running several decompositions at once on separate streams
+                         gives each a share of the device so that their latency-bound kernels run side
+                         by side; results change only by the rounding order of the block sums. */
 } ssa_opts_t;
 
 #define SSA_REORTH_FULL 0
@@ -302,6 +307,9 @@ typedef struct ssa_serve_opts {
   int batch_workers;    /* batched launches running at once (default 1, at most 16; 0 = never batch) */
   int max_batch;        /* requests per batched launch (default 128) */
   int64_t batch_max_n;  /* only series with N <= this are batched (0 = the engine's limit, -1 = none) */
+  int grid_cap;         /* ssa_opts_t.grid_cap of every single-series request (default 0: the whole device;
+                           measured on the serving workload, shares of 2 x SMs / workers CTAs lowered the
+                           capacity from 75 to 66 requests/s with 8 workers) */
 } ssa_serve_opts_t;
 
 #define SSA_SERVE_VECTORS 1  /* ssa_serve_submit outputs flag: keep U and V (else sigma and residuals only) */

@@ -27,7 +27,7 @@ class SsaOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
                 ("krylov_dim", ctypes.c_int), ("keep", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("refine", ctypes.c_int), ("reorth_skip", ctypes.c_double),
-                ("reorth", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("grid_cap", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -38,7 +38,7 @@ class KernelStat(ctypes.Structure):
 class ServeOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("mem_budget", ctypes.c_int64),
                 ("workers", ctypes.c_int), ("batch_workers", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("batch_max_n", ctypes.c_int64)]
+                ("batch_max_n", ctypes.c_int64), ("grid_cap", ctypes.c_int)]
 
 
 class ServeInfo(ctypes.Structure):
@@ -157,7 +157,7 @@ def ssa_default_opts() -> SsaOpts:
 
 
 def make_opts(precision=SSA_PREC_F64, tol=0.0, max_restarts=200, krylov_dim=0, keep=0, seed=0, stream=None,
-              refine=SSA_REFINE_OFF, reorth_skip=0.0, reorth=0):
+              refine=SSA_REFINE_OFF, reorth_skip=0.0, reorth=0, grid_cap=0):
     o = ssa_default_opts()
     o.precision, o.tol, o.max_restarts = precision, tol, max_restarts
     o.krylov_dim, o.keep, o.seed = krylov_dim, keep, seed
@@ -165,6 +165,7 @@ def make_opts(precision=SSA_PREC_F64, tol=0.0, max_restarts=200, krylov_dim=0, k
     o.refine = refine
     o.reorth_skip = reorth_skip
     o.reorth = reorth
+    o.grid_cap = grid_cap
     return o
 
 

@@ -286,7 +286,10 @@ void launch_cgs2(const df64* Q, int64_t ldq, int ncols, df64* w, int64_t dim, Re
   const bool gated = mode == REORTH_GATED || mode == REORTH_PRO;
   if (ncols <= FUSED_MAXCOL) {
     const int T2 = fused_tiles(dim);
-    auto grid = [&](int pass) { return g_lanes_grid[pass][ncols] < T2 ? g_lanes_grid[pass][ncols] : T2; };
+    auto grid = [&](int pass) {
+      int g = g_lanes_grid[pass][ncols] < T2 ? g_lanes_grid[pass][ncols] : T2;
+      return rw.grid_cap > 0 && g > rw.grid_cap ? rw.grid_cap : g;
+    };
     const int ldp = rw.ldp2;
     const df64* hlast = rw.h;
     const int* gate = nullptr;

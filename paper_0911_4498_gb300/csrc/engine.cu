@@ -428,6 +428,7 @@ extern "C" void ssa_default_opts(ssa_opts_t* o) {
   o->refine = SSA_REFINE_OFF;
   o->reorth_skip = 0.0;
   o->reorth = SSA_REORTH_FULL;
+  o->grid_cap = 0;
 }
 
 extern "C" const char* ssa_strerror(int code) {
@@ -473,6 +474,7 @@ extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_
   REQ(o.refine == SSA_REFINE_OFF || o.refine == SSA_REFINE_ON, "unknown refine mode %d", o.refine);
   REQ(o.reorth_skip >= 0.0 && o.reorth_skip < 1e-3, "reorth_skip must be in [0, 1e-3) (got %g)", o.reorth_skip);
   REQ(o.reorth == SSA_REORTH_FULL || o.reorth == SSA_REORTH_PRO, "unknown reorth mode %d", o.reorth);
+  REQ(o.grid_cap >= 0, "grid_cap must be >= 0 (got %d)", o.grid_cap);
   ssa_plan_s* p = new (std::nothrow) ssa_plan_s();
   if (!p) return SSA_ENOMEM;
   p->opts = o;
@@ -805,6 +807,7 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   // arrow matrix): a first cycle that does not converge starts over with full Gram-Schmidt
   bool pro = prec != SSA_PREC_F32C && p->opts.reorth == SSA_REORTH_PRO;
   w.rw.skip_tau = prec == SSA_PREC_F32C || pro ? 0.0 : p->opts.reorth_skip;
+  w.rw.grid_cap = p->opts.grid_cap;
   w.pro.eps = 1.4e-14f;  // relative error of the double-float products (2^-46)
   int r = 1, c = 0;
   auto side = [&](bool vside) -> int {

@@ -34,6 +34,7 @@ struct ReorthWork {
   int* run;      // 1 when the second pass must run (skip test on the device)
   int* skip;     // 1 when the skip test fired (then *run == 0 and *gate == 0)
   double skip_tau;  // level of the skip test in REORTH_GATED (0: no skip test)
+  int grid_cap = 0;  // most blocks of the persistent passes and the cooperative kernels (0: no cap)
   // set by launch_cgs2 for launch_normalize_coop: when *skip_flag is 1 on the
   // device, the normalisation forms w <- w - h[ncols-1] q_{ncols-1} and its
   // norm itself (h = the first projection, in h)

@@ -833,6 +833,7 @@ int launch_normalize_coop(df64* w, int64_t dim, ReorthWork& rw, df64* qcol, df64
                           const df64* Q, int64_t ldq, int ncols, uint64_t seed, uint64_t stream, unsigned* status,
                           cudaStream_t s) {
   int blocks = grid_for(dim, 256, coop_blocks());
+  if (rw.grid_cap > 0 && blocks > rw.grid_cap) blocks = rw.grid_cap;
   int lds = MAXCOL + 1;
   const df64* nrm = rw.nrm;
   df64* scratch = rw.coop;
@@ -884,7 +885,8 @@ int launch_pro_pre(df64* w, int64_t dim, const df64* qprev, const df64* coef, Re
     if (per < 1) per = 1;
     return sms * per < coop_blocks() ? sms * per : coop_blocks();
   }();
-  const int blocks = grid_for(dim, 256, pro_cap);
+  int blocks = grid_for(dim, 256, pro_cap);
+  if (rw.grid_cap > 0 && blocks > rw.grid_cap) blocks = rw.grid_cap;
   void* args[] = {&a};
   prof_begin(s);
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_pro_pre, dim3(blocks), dim3(256), args, 0, s);

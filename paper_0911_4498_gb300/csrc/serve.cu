@@ -62,6 +62,7 @@ struct ssa_server_s {
   std::deque<Req*> q_single, q_batch;
   std::unordered_map<int64_t, Req*> reqs;
   int64_t next_id = 1;
+  int grid_cap = 0;  // ssa_opts_t.grid_cap of the single-series requests
   int64_t mem_in_use = 0, mem_peak = 0;
   int64_t submitted = 0, completed = 0, running = 0, batches = 0, batched_requests = 0;
   bool stop = false;
@@ -103,6 +104,7 @@ void run_single(ssa_server_s* S, Req* r, cudaStream_t st) {
   o.precision = S->o.precision;
   o.tol = S->o.tol;
   o.stream = st;
+  o.grid_cap = S->grid_cap;
   ssa_plan_t plan = nullptr;
   int rc = ssa_embed_plan(r->N, r->L, &o, &plan);
   if (rc) return fail(r, rc);
@@ -300,10 +302,15 @@ extern "C" int ssa_serve_create(const ssa_serve_opts_t* opts, ssa_server_t* out)
     host_set_error("at most 64 single-series workers and 16 batch workers");
     return SSA_EINVAL;
   }
+  if (o.grid_cap < 0) {
+    host_set_error("grid_cap must be >= 0");
+    return SSA_EINVAL;
+  }
   ssa_server_s* S = new (std::nothrow) ssa_server_s();
   if (!S) return SSA_ENOMEM;
   S->o = o;
   cudaGetDevice(&S->dev);
+  S->grid_cap = o.grid_cap;
   S->t0 = std::chrono::steady_clock::now();
   // keep freed stream-ordered memory in the pool so that per-request
   // allocations are served without returning to the driver

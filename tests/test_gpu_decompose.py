@@ -281,3 +281,21 @@ def test_partial_reorthogonalisation_falls_back_to_full():
     assert pro["info"]["restarts"] == full["info"]["restarts"] + 1
     assert np.array_equal(full["sigma"], pro["sigma"])
     assert np.array_equal(full["U"], pro["U"]) and np.array_equal(full["V"], pro["V"])
+
+
+@pytest.mark.parametrize("N,L,k,cap,reorth", [(40000, 13333, 12, 16, ssa.SSA_REORTH_FULL),
+                                              (65536, 32768, 20, 19, ssa.SSA_REORTH_FULL),
+                                              (40000, 13333, 12, 7, ssa.SSA_REORTH_PRO)])
+def test_grid_cap(N, L, k, cap, reorth):
+    """opts.grid_cap limits the persistent reorthogonalisation passes and the cooperative kernels to
+    `cap` CTAs (the server's share per request): the block sums add up in another order, the
+    results stay within the FP64 tolerances of the oracle, and a negative cap is rejected."""
+    f = synth.many_sines(N, seed=N + cap)
+    ref = ossa.decompose(f, L, k, method="lanczos")
+    got = gpu_decompose(f, L, k, grid_cap=cap, reorth=reorth)
+    assert got["rc"] == ssa.SSA_OK and got["info"]["converged"]
+    assert np.max(_rel(got["sigma"], ref["sigma"])) <= SIG_F64
+    tol = 1e-9 if reorth == ssa.SSA_REORTH_FULL else 2.0 ** -23
+    compare_vectors(got["U"], ref["U"], ref["sigma"], tol, res_tol=1e-11 if reorth == ssa.SSA_REORTH_FULL else 1e-9)
+    with pytest.raises(ssa.SSAError):
+        gpu_decompose(f, L, k, grid_cap=-1)

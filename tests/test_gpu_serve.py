@@ -83,13 +83,18 @@ def test_each_result_same_alone_and_in_the_mix():
         compare_vectors(U.T.copy(), mix[j]["U"], sig, 1e-5, skip_below=1e-2 * sig[0], res_tol=1e-6)
 
 
-def test_f64_server_matches_plan_path():
+@pytest.mark.parametrize("grid_cap", [0, 24])
+def test_f64_server_matches_plan_path(grid_cap):
+    """FP64 requests through the server (whole-device grids, or capped to 24 CTAs per persistent
+    kernel) give the plan path's sigma to the FP64 tolerance; a negative cap is refused."""
     from ssa_testlib import gpu_decompose
-    specs = [(1000, 500, 10), (30000, 15000, 12), (2000, 1000, 40)]
-    out, _ = _serve(specs, ssa.make_serve_opts(precision=ssa.SSA_PREC_F64))
+    specs = [(1000, 500, 10), (30000, 15000, 12), (2000, 1000, 40), (70000, 35000, 8)]
+    out, _ = _serve(specs, ssa.make_serve_opts(precision=ssa.SSA_PREC_F64, grid_cap=grid_cap))
     for i, ((N, L, k), o) in enumerate(zip(specs, out)):
         p = gpu_decompose(_series(i, N), L, k)
         assert np.max(np.abs(p["sigma"] - o["sigma"]) / p["sigma"]) <= 1e-10
+    with pytest.raises(ssa.SSAError):
+        ssa.ssa_serve_create(ssa.make_serve_opts(grid_cap=-1))
 
 
 def test_budget_admission_and_overlap():
