@@ -94,7 +94,15 @@ typedef struct ssa_opts {
                          coefficients it leaves out would spoil a thick restart, so a first cycle that
                          does not converge starts over from the same starting vector with full
                          Gram-Schmidt (counted as one restart): choose krylov_dim large enough for one
-                         cycle.  reorth_skip is ignored in this mode. */
+                         cycle.  reorth_skip is ignored in this mode.
+                         SSA_REORTH_NONE (SSA_PREC_F64 only): no reorthogonalisation (section 3.2.1): one
+                         cycle of krylov_dim steps (default four times the usual 2k or k + 32, at most
+                         510) with no Gram-Schmidt and no restart; the singular values of the projected
+                         matrix are filtered by the Cullum-Willoughby test (a simple value that is also a
+                         singular value of the projected matrix without its first row is spurious; copies
+                         count once), and the first k that pass are returned with unit Ritz vectors.
+                         Accuracy is not FP64-class in general: converged means k values passed with
+                         residual estimates <= tol sigma_1, else SSA_ENOCONV. */
   int grid_cap;       /* most CTAs of one launch of the persistent reorthogonalisation passes and the
                          cooperative normalisation (0, default: as many as are resident on the whole
                          device).  A caller running several decompositions at once on separate streams
@@ -104,6 +112,7 @@ typedef struct ssa_opts {
 
 #define SSA_REORTH_FULL 0
 #define SSA_REORTH_PRO 1
+#define SSA_REORTH_NONE 2
 
 #define SSA_REFINE_OFF 0
 #define SSA_REFINE_ON 1

@@ -9,7 +9,7 @@ synthetic workloads.
 """
 from ._lib import (ssa_batch_destroy, ssa_batch_get, ssa_batch_info, ssa_batch_plan, ssa_batch_reconstruct,
                    ssa_batch_run, ssa_batch_wait, ssa_decompose_batch,  # noqa: F401
-                   SSA_ENOCONV, SSA_ENOMEM, SSA_OK, SSA_PREC_F32C, SSA_PREC_F64, SSA_REFINE_OFF, SSA_REFINE_ON, SSA_REORTH_FULL, SSA_REORTH_PRO,
+                   SSA_ENOCONV, SSA_ENOMEM, SSA_OK, SSA_PREC_F32C, SSA_PREC_F64, SSA_REFINE_OFF, SSA_REFINE_ON, SSA_REORTH_FULL, SSA_REORTH_NONE, SSA_REORTH_PRO,
                    SSAError, groups_csr, lib, make_opts,
                    ssa_decomp_destroy, ssa_decomp_get, ssa_decomp_info, ssa_decompose, ssa_default_opts,
                    ssa_embed_plan, ssa_fft_threads, ssa_fft_tiling, ssa_get_spectrum, ssa_hankelize, ssa_hmatrix, ssa_last_error, ssa_matvec, ssa_matvec_noalloc,

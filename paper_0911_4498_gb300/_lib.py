@@ -20,7 +20,7 @@ SSA_OK, SSA_EINVAL, SSA_ENOMEM, SSA_ENOCONV = range(4)
 SSA_ECUDA, SSA_ENUMERIC = 5, 6
 SSA_PREC_F64, SSA_PREC_F32C = 0, 1
 SSA_REFINE_OFF, SSA_REFINE_ON = 0, 1
-SSA_REORTH_FULL, SSA_REORTH_PRO = 0, 1
+SSA_REORTH_FULL, SSA_REORTH_PRO, SSA_REORTH_NONE = 0, 1, 2
 
 
 class SsaOpts(ctypes.Structure):

@@ -204,6 +204,7 @@ struct Workspace {
   df64* y = nullptr;
   ReorthWork rw{};
   SvdWork sw{};
+  SvdWork sw2{};  // ghost filtering: the projected matrix without its first row
   df64* est = nullptr;
   df64* dummy = nullptr;
   int* flag = nullptr;
@@ -232,6 +233,17 @@ struct Workspace {
     free_async(rw.skip, st);
     free_async(rw.nrm, st);
     free_async(rw.counter, st);
+    for (SvdWork* v : {&sw2}) {
+      free_async(v->A, st);
+      free_async(v->W, st);
+      free_async(v->sigma, st);
+      free_async(v->P, st);
+      free_async(v->Q, st);
+      free_async(v->resid, st);
+      free_async(v->sigma_d, st);
+      free_async(v->conv, st);
+      *v = SvdWork{};
+    }
     free_async(sw.A, st);
     free_async(sw.W, st);
     free_async(sw.sigma, st);
@@ -473,7 +485,8 @@ extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_
   REQ(o.precision == SSA_PREC_F64 || o.precision == SSA_PREC_F32C, "unknown precision %d", o.precision);
   REQ(o.refine == SSA_REFINE_OFF || o.refine == SSA_REFINE_ON, "unknown refine mode %d", o.refine);
   REQ(o.reorth_skip >= 0.0 && o.reorth_skip < 1e-3, "reorth_skip must be in [0, 1e-3) (got %g)", o.reorth_skip);
-  REQ(o.reorth == SSA_REORTH_FULL || o.reorth == SSA_REORTH_PRO, "unknown reorth mode %d", o.reorth);
+  REQ(o.reorth == SSA_REORTH_FULL || o.reorth == SSA_REORTH_PRO || o.reorth == SSA_REORTH_NONE,
+      "unknown reorth mode %d", o.reorth);
   REQ(o.grid_cap >= 0, "grid_cap must be >= 0 (got %d)", o.grid_cap);
   ssa_plan_s* p = new (std::nothrow) ssa_plan_s();
   if (!p) return SSA_ENOMEM;
@@ -754,6 +767,16 @@ static int ensure_workspace(ssa_plan_t p, int d) {
   CK(malloc_async(&w.sw.resid, cols * sizeof(double), st));
   CK(malloc_async(&w.sw.sigma_d, cols * sizeof(double), st));
   CK(malloc_async(&w.sw.conv, sizeof(int), st));
+  if (p->opts.reorth == SSA_REORTH_NONE) {
+    CK(malloc_async(&w.sw2.A, sq, st));
+    CK(malloc_async(&w.sw2.W, sq, st));
+    CK(malloc_async(&w.sw2.P, sq, st));
+    CK(malloc_async(&w.sw2.Q, sq, st));
+    CK(malloc_async(&w.sw2.sigma, cols * sizeof(df64), st));
+    CK(malloc_async(&w.sw2.resid, cols * sizeof(double), st));
+    CK(malloc_async(&w.sw2.sigma_d, cols * sizeof(double), st));
+    CK(malloc_async(&w.sw2.conv, sizeof(int), st));
+  }
   CK(malloc_async(&w.est, sizeof(df64), st));
   CK(malloc_async(&w.dummy, sizeof(df64), st));
   CK(malloc_async(&w.flag, sizeof(int), st));
@@ -770,11 +793,86 @@ static int ensure_workspace(ssa_plan_t p, int d) {
 
 static int refine_sigma(ssa_plan_t p, ssa_decomp_s* res, int k);
 
+// Cullum-Willoughby filtering of a bidiagonalisation run without reorthogonalisation
+// (section 3.2.1): the projected matrix B (r x c) is the Golub-Kahan tridiagonal of the
+// Lanczos process started from u_1; a simple singular value of B that is also a singular
+// value of B without its first row is spurious, and copies of a value count once (the copy
+// with the smallest residual is kept).  The first k values that pass become the first k
+// columns of the SVD outputs (P, Q, sigma, residuals), in descending order; when fewer than
+// k pass, the largest remaining values fill the rest and the result is not converged.  converged: k values passed and each residual
+// is <= tol sigma_1.
+static int ghost_filter(Workspace& w, int r, int c, int k, double tol, int* converged, cudaStream_t s) {
+  w.sw2.max_sweeps = w.sw.max_sweeps;
+  w.sw2.rot_tol = w.sw.rot_tol;
+  launch_small_svd(w.B + w.ldb, w.ldb, r - 1, c, w.sw2, 0, 1.0, w.est, w.status, s);
+  CHECK_LAUNCH();
+  std::vector<double> sig(c), sig2(c), res(c);
+  CK(cudaMemcpyAsync(sig.data(), w.sw.sigma_d, c * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(sig2.data(), w.sw2.sigma_d, c * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(res.data(), w.sw.resid, c * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double same = 1e-10 * sig[0];  // two singular values agree within this
+  std::vector<int> keep;
+  for (int i = 0; i < c && (int)keep.size() < k && sig[i] > same;) {
+    int j = i;
+    while (j + 1 < c && sig[j + 1] >= sig[i] - same) ++j;
+    bool spurious = false;
+    if (j == i)
+      for (int t = 0; t < c; ++t)
+        if (std::fabs(sig2[t] - sig[i]) <= same) spurious = true;
+    if (!spurious) {  // of several copies, the one whose Ritz pair has the smallest residual
+      int best = i;
+      for (int t = i + 1; t <= j; ++t)
+        if (res[t] < res[best]) best = t;
+      keep.push_back(best);
+    }
+    i = j + 1;
+  }
+  bool ok = (int)keep.size() == k;
+  for (int i : keep) ok = ok && res[i] <= tol * sig[0];
+  std::vector<char> used(c, 0);
+  for (int i : keep) used[i] = 1;
+  for (int i = 0; i < c && (int)keep.size() < k; ++i)
+    if (!used[i]) keep.push_back(i);
+  std::sort(keep.begin(), keep.end());
+  *converged = ok ? 1 : 0;
+  // gather the kept columns into the first k places (host round trip of the small matrices)
+  std::vector<df64> P((size_t)r * c), Q((size_t)c * c), sg(c);
+  std::vector<double> sd(c);
+  CK(cudaMemcpyAsync(P.data(), w.sw.P, P.size() * sizeof(df64), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(Q.data(), w.sw.Q, Q.size() * sizeof(df64), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(sg.data(), w.sw.sigma, c * sizeof(df64), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(sd.data(), w.sw.sigma_d, c * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<df64> P2((size_t)r * k), Q2((size_t)c * k), sg2(k);
+  std::vector<double> sd2(k), res2(k);
+  for (int m = 0; m < k; ++m) {
+    const int i = keep[m];
+    std::copy(P.begin() + (size_t)i * r, P.begin() + (size_t)(i + 1) * r, P2.begin() + (size_t)m * r);
+    std::copy(Q.begin() + (size_t)i * c, Q.begin() + (size_t)(i + 1) * c, Q2.begin() + (size_t)m * c);
+    sg2[m] = sg[i];
+    sd2[m] = sd[i];
+    res2[m] = res[i];
+  }
+  CK(cudaMemcpyAsync(w.sw.P, P2.data(), P2.size() * sizeof(df64), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.sw.Q, Q2.data(), Q2.size() * sizeof(df64), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.sw.sigma, sg2.data(), k * sizeof(df64), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.sw.sigma_d, sd2.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.sw.resid, res2.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  return SSA_OK;
+}
+
 static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   const int prec = p->opts.precision;
   const int64_t Lw = p->Lw, Kw = p->Kw;
   const int64_t mn = Lw < Kw ? Lw : Kw;
+  const bool none = prec != SSA_PREC_F32C && p->opts.reorth == SSA_REORTH_NONE;
   int d = p->opts.krylov_dim > 0 ? p->opts.krylov_dim : (2 * k > k + 32 ? 2 * k : k + 32);
+  // without reorthogonalisation one cycle of four times the usual length (copies of the converged
+  // triples take up part of it; three times left the last residuals near 2e-12 sigma_1 at
+  // k = 12-16), within the largest basis
+  if (none && p->opts.krylov_dim <= 0) d = 4 * d < MAXCOL - 2 ? 4 * d : MAXCOL - 2;
   if (d > mn) d = (int)mn;
   if (d < k) d = k;
   REQ(d <= MAXCOL - 2, "Krylov dimension %d exceeds %d", d, MAXCOL - 2);
@@ -821,6 +919,22 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     launch_matvec_df(p->g, prec, vside ? 1 : 0, src, 0, w.y, 0, 1, p->chat, p->scratch, s);
     ++matvecs;
     int mode = reorth;
+    if (none && ncols > 0) {
+      // no reorthogonalisation (section 3.2.1): the recurrence's one coupling and ||w||^2
+      CK((cudaError_t)launch_pro_pre(w.y, dim, vside ? V + (int64_t)(c - 1) * w.ldv : U + (int64_t)(r - 1) * w.ldu,
+                                     w.B + (int64_t)(r - 1) * w.ldb + (c - 1), w.rw, w.pro, w.B, w.ldb,
+                                     vside ? 1 : 0, ncols, vside ? r - 1 : c - 1, 0, 0, -1, w.est, s));
+      w.rw.nrm_blocks = 0;  // the normalisation takes *rw.nrm
+      w.rw.skip_flag = nullptr;
+      df64* qcol = Qb + (int64_t)ncols * ldq;
+      CK((cudaError_t)launch_normalize_coop(w.y, dim, w.rw, qcol, bentry, w.est, Qb, ldq, ncols, seed, stream_id,
+                                            w.status, s));
+      ++stream_id;
+      CHECK_LAUNCH();
+      if (vside) ++c;
+      else ++r;
+      return SSA_OK;
+    }
     if (pro && ncols > 0) {
       // partial reorthogonalisation (first cycle only): subtract the one known coupling B[r-1][c-1]
       // (to v_{c-1} on the v side, to u_{r-1} on the u side), update the estimates and decide on
@@ -845,7 +959,7 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   auto start = [&]() -> int {
     CK(cudaMemsetAsync(w.B, 0, (size_t)w.ldb * w.ldb * sizeof(df64), s));
     CK(cudaMemsetAsync(w.est, 0, sizeof(df64), s));
-    if (pro) launch_pro_reset(w.pro, s);
+    if (pro || none) launch_pro_reset(w.pro, s);
     launch_random_fill(w.y, Lw, seed, 0, s);
     launch_cgs2(U, w.ldu, 0, w.y, Lw, w.rw, reorth, s);
     CK((cudaError_t)launch_normalize_coop(w.y, Lw, w.rw, U, w.dummy, w.est, U, w.ldu, 0, seed, stream_id++,
@@ -883,6 +997,11 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
       set_err("non-finite value in the Lanczos recurrence");
       return SSA_ENUMERIC;
     }
+    if (none) {  // one cycle, then the Cullum-Willoughby filter picks the k triples
+      rc = ghost_filter(w, r, cp, k, tol, &converged, s);
+      if (rc) return rc;
+      break;
+    }
     if (converged || restarts >= p->opts.max_restarts || kk >= cp) break;
     if (pro) {  // the first cycle did not converge: start over with full Gram-Schmidt
       pro = false;
@@ -912,6 +1031,10 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   const int cp = c - 1;
   launch_ritz(U, w.ldu, r, w.sw.P, r, k, Uf, w.ldu, Lw, s);
   launch_ritz(V, w.ldv, cp, w.sw.Q, cp, k, Vf, w.ldv, Kw, s);
+  if (none) {  // the bases are not orthonormal: unit Ritz vectors
+    launch_normalize_cols(Uf, w.ldu, Lw, k, s);
+    launch_normalize_cols(Vf, w.ldv, Kw, k, s);
+  }
   CHECK_LAUNCH();
   // sign rule on the user's left vectors
   const df64* Uuser = p->transposed ? Vf : Uf;

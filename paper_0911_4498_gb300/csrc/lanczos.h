@@ -107,6 +107,8 @@ void launch_restart_B(df64* B, int ldb, int nrows_clear, const SvdWork& sw, int 
 void launch_ritz(const df64* Q, int64_t ldq, int r, const df64* P, int ldp, int ncol, df64* out, int64_t ldo,
                  int64_t dim, cudaStream_t s);
 void launch_copy_df(const df64* src, df64* dst, int64_t n, cudaStream_t s);
+// Q[:, j] /= ||Q[:, j]||, j < ncol (one block per column)
+void launch_normalize_cols(df64* Q, int64_t ldq, int64_t dim, int ncol, cudaStream_t s);
 void launch_sign(const df64* U, int64_t ldu, int64_t dim, int k, int* sgn, cudaStream_t s);
 void launch_store_cols(const df64* src, int64_t lds, int64_t dim, int ncol, const int* sgn, double* dst, int64_t ldd,
                        cudaStream_t s);

@@ -765,6 +765,24 @@ __global__ void k_sign(const df64* __restrict__ U, int64_t ldu, int64_t dim, int
   if (threadIdx.x == 0) sgn[j] = u[si[0]].hi < 0.f ? -1 : 1;
 }
 
+// Q[:, j] /= ||Q[:, j]|| in place, one block per column (Ritz vectors of a basis
+// that is not orthonormal)
+__global__ void __launch_bounds__(256) k_normalize_cols(df64* __restrict__ Q, int64_t ldq, int64_t dim) {
+  __shared__ df64 sh[32];
+  __shared__ df64 s_inv;
+  df64* q = Q + (int64_t)blockIdx.x * ldq;
+  df64 acc = df_zero();
+  for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) acc = df_fma(q[i], q[i], acc);
+  acc = block_sum_df(acc, sh);
+  if (threadIdx.x == 0) {
+    const df64 nrm = df_sqrt(acc);
+    s_inv = nrm.hi > 0.f ? df_div(make_df(1.f, 0.f), nrm) : make_df(1.f, 0.f);
+  }
+  __syncthreads();
+  const df64 inv = s_inv;
+  for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) q[i] = df_mul(q[i], inv);
+}
+
 // dst[:, j] = sgn[j] * src[:, j] as doubles
 __global__ void k_store_cols(const df64* __restrict__ src, int64_t lds, int64_t dim, int ncol,
                              const int* __restrict__ sgn, double* __restrict__ dst, int64_t ldd) {
@@ -1012,6 +1030,13 @@ void launch_sign(const df64* U, int64_t ldu, int64_t dim, int k, int* sgn, cudaS
   prof_begin(s);
   k_sign<<<k, 1024, 0, s>>>(U, ldu, dim, sgn);
   prof_end(s, K_MISC, 8.0 * (double)dim * k, 0.0);
+}
+
+void launch_normalize_cols(df64* Q, int64_t ldq, int64_t dim, int ncol, cudaStream_t s) {
+  if (ncol <= 0) return;
+  prof_begin(s);
+  k_normalize_cols<<<ncol, 256, 0, s>>>(Q, ldq, dim);
+  prof_end(s, K_MISC, 16.0 * (double)dim * ncol, 0.0);
 }
 
 void launch_store_cols(const df64* src, int64_t lds, int64_t dim, int ncol, const int* sgn, double* dst, int64_t ldd,

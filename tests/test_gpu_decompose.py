@@ -12,6 +12,8 @@ from oracle import trajectory
 from paper_0911_4498_gb300 import synth
 from ssa_testlib import compare_vectors, gpu_decompose, gpu_decompose_reconstruct
 
+from conftest import load_golden
+
 pytestmark = pytest.mark.gpu
 
 SIG_F64 = 1e-10     # sigma relative error, FP64-class path
@@ -299,3 +301,43 @@ def test_grid_cap(N, L, k, cap, reorth):
     compare_vectors(got["U"], ref["U"], ref["sigma"], tol, res_tol=1e-11 if reorth == ssa.SSA_REORTH_FULL else 1e-9)
     with pytest.raises(ssa.SSAError):
         gpu_decompose(f, L, k, grid_cap=-1)
+
+
+@pytest.mark.parametrize("N,L,k", [(5000, 2500, 8), (5000, 2500, 16), (40000, 13333, 12)])
+def test_no_reorthogonalisation_with_ghost_filter(N, L, k):
+    """SSA_REORTH_NONE (section 3.2.1): one cycle of 4 x the usual length with no Gram-Schmidt,
+    spurious copies removed by the Cullum-Willoughby test.  Where the cycle converges the k
+    leading triples, sigma agree with the oracle's to the FP64 tolerance (measured <= 1.5e-14),
+    the unit Ritz vectors to 1e-6 (measured <= 2.2e-8: without reorthogonalisation they are
+    accurate only as far as the converged copies reach) and the reconstructions of the leading
+    components to 1e-8 (measured <= 1.8e-10)."""
+    f = synth.many_sines(N, seed=N)
+    ref = ossa.decompose(f, L, k, method="lanczos")
+    groups = [[0], [1], [2, 3]]
+    got = gpu_decompose_reconstruct(f, L, k, groups, reorth=ssa.SSA_REORTH_NONE)
+    assert got["rc"] == ssa.SSA_OK and got["info"]["converged"] and got["info"]["restarts"] == 0
+    assert got["info"]["krylov_dim"] == 4 * max(2 * k, k + 32)
+    assert np.max(_rel(got["sigma"], ref["sigma"])) <= SIG_F64
+    compare_vectors(got["U"], ref["U"], ref["sigma"], 1e-6)
+    compare_vectors(got["V"], ref["V"], ref["sigma"], 1e-6)
+    for Q in (got["U"], got["V"]):
+        assert np.max(np.abs(np.linalg.norm(Q, axis=0) - 1.0)) <= 1e-13
+    rec_ref = ossa.reconstruct(N, L, ref["sigma"], ref["U"], ref["V"], groups, method="fft", fft="library")
+    for gi in range(len(groups)):
+        err = np.linalg.norm(got["rec"][gi] - rec_ref[gi]) / np.linalg.norm(rec_ref[gi])
+        assert err <= 1e-8, (gi, err)
+
+
+def test_no_reorthogonalisation_reports_what_it_misses():
+    """k = 100 at N = 5113: the longest cycle allowed (510 steps) does not converge the tail
+    without reorthogonalisation; the call returns SSA_ENOCONV with k finite values in descending
+    order, the leading ones still right."""
+    N, L, k = 5113, 2556, 100
+    f = synth.three_sines(N, seed=7)
+    got = gpu_decompose(f, L, k, reorth=ssa.SSA_REORTH_NONE)
+    assert got["rc"] == ssa.SSA_ENOCONV and not got["info"]["converged"]
+    assert got["info"]["krylov_dim"] == 510
+    s = got["sigma"]
+    assert np.all(np.isfinite(s)) and np.all(np.diff(s) <= 0)
+    ref = load_golden("sigma_three_sines_N5113_L2556_k100.txt")["sigma"]
+    assert np.max(np.abs(s[:10] - ref[:10]) / ref[:10]) <= SIG_F64
