@@ -64,6 +64,39 @@ static bool is_device_ptr(const void* p) {
 // after them fails as if the device were out of memory, without calling the
 // allocator; then the injection disarms itself.
 static std::atomic<int64_t> g_fail_after{-1};
+// The library's stream-ordered allocations come from its own memory pool on each device, which
+// keeps up to 4 GiB of freed memory for reuse.  The device's default pool hands freed memory
+// back to the driver at every synchronisation, so the per-call scratch of the reconstruction
+// (about 1.3 GB at N = 2^20) and host-output staging were mapped again on every call.
+static cudaMemPool_t lib_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  static bool tried[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!tried[dev]) {
+    tried[dev] = true;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+      uint64_t keep = (uint64_t)4 << 30;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      pools[dev] = pool;
+    } else {
+      cudaGetLastError();  // fall back to the default pool
+    }
+  }
+  return pools[dev];
+}
+
 template <class T> static cudaError_t dev_alloc(T** ptr, size_t bytes, cudaStream_t s) {
   int64_t v = g_fail_after.load();
   while (v >= 0) {
@@ -75,6 +108,8 @@ template <class T> static cudaError_t dev_alloc(T** ptr, size_t bytes, cudaStrea
       break;
     }
   }
+  cudaMemPool_t pool = lib_pool();
+  if (pool) return cudaMallocFromPoolAsync(reinterpret_cast<void**>(ptr), bytes, pool, s);
   return cudaMallocAsync(reinterpret_cast<void**>(ptr), bytes, s);
 }
 
