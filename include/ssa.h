@@ -411,6 +411,22 @@ uint64_t ssa_kernel_launches(void);
  */
 int ssa_fault_inject_alloc(int64_t after);
 
+/*
+ * The ghost filter of SSA_REORTH_NONE on the host (no device access), exposed so that it can be
+ * checked on its own (section 3.2.1, the Cullum-Willoughby test).  sigma: the c singular values of
+ * the projected matrix B in descending order; sigma_hat: the c_hat singular values of B without its
+ * first row; resid: the residual estimates of sigma's Ritz pairs.  Two values agree when they
+ * differ by at most 1e-10 sigma[0]; values at or below that are not candidates.  Walking sigma's
+ * groups of agreeing values in descending order, a group of one value that agrees with a sigma_hat
+ * value is spurious; any other group keeps its member with the smallest residual.  keep (k
+ * entries, caller-owned) receives the first k kept indices in ascending order, padded with the
+ * largest unused indices when fewer pass; *converged = 1 when k passed and every kept residual is
+ * <= tol sigma[0].  Errors: SSA_EINVAL (NULL pointer, k outside [1, c], sigma not descending,
+ * non-finite input).
+ */
+int ssa_cw_filter(const double* sigma, int c, const double* sigma_hat, int c_hat, const double* resid, int k,
+                  double tol, int32_t* keep, int* converged);
+
 /* ---- allocation-free product (no counterpart in the paper) -------------- */
 
 /*

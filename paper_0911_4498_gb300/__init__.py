@@ -15,6 +15,6 @@ from ._lib import (ssa_batch_destroy, ssa_batch_get, ssa_batch_info, ssa_batch_p
                    ssa_embed_plan, ssa_fft_threads, ssa_fft_tiling, ssa_get_spectrum, ssa_hankelize, ssa_hmatrix, ssa_last_error, ssa_matvec, ssa_matvec_noalloc,
                    ssa_plan_destroy,
                    ssa_plan_info, ssa_reconstruct, ssa_set_series, ssa_stats_enable, ssa_stats_get,
-                   ssa_kernel_launches, ssa_fault_inject_alloc, ssa_strerror, SSA_SERVE_VECTORS, make_serve_opts, ssa_serve_create,
+                   ssa_kernel_launches, ssa_fault_inject_alloc, ssa_cw_filter, ssa_strerror, SSA_SERVE_VECTORS, make_serve_opts, ssa_serve_create,
                    ssa_serve_default_opts, ssa_serve_destroy, ssa_serve_poll, ssa_serve_stats, ssa_serve_submit,
                    ssa_serve_take)

@@ -102,6 +102,7 @@ _SIGS = {
     "ssa_stats_get": (_I, [ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "ssa_kernel_launches": (ctypes.c_uint64, []),
     "ssa_fault_inject_alloc": (_I, [_I64]),
+    "ssa_cw_filter": (_I, [_VP, _I, _VP, _I, _VP, _I, _D, _VP, ctypes.POINTER(_I)]),
     "ssa_strerror": (ctypes.c_char_p, [_I]),
     "ssa_last_error": (ctypes.c_char_p, []),
 }
@@ -395,3 +396,17 @@ def groups_csr(groups):
         idx.extend(int(i) for i in members)
         off[g + 1] = len(idx)
     return off, np.array(idx if idx else [0], dtype=np.int32)
+
+
+def ssa_cw_filter(sigma, sigma_hat, resid, k: int, tol: float):
+    """Host-side Cullum-Willoughby selection: (kept indices, converged)."""
+    import numpy as np
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    sigma_hat = np.ascontiguousarray(sigma_hat, dtype=np.float64)
+    resid = np.ascontiguousarray(resid, dtype=np.float64)
+    keep = np.zeros(k, dtype=np.int32)
+    conv = _I()
+    _check(lib().ssa_cw_filter(sigma.ctypes.data, int(sigma.size), sigma_hat.ctypes.data if sigma_hat.size else None,
+                               int(sigma_hat.size), resid.ctypes.data, int(k), float(tol), keep.ctypes.data,
+                               ctypes.byref(conv)))
+    return keep, bool(conv.value)

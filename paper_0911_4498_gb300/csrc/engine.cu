@@ -522,6 +522,8 @@ extern "C" int ssa_embed_plan(int64_t N, int64_t L, const ssa_opts_t* opts, ssa_
   REQ(o.reorth_skip >= 0.0 && o.reorth_skip < 1e-3, "reorth_skip must be in [0, 1e-3) (got %g)", o.reorth_skip);
   REQ(o.reorth == SSA_REORTH_FULL || o.reorth == SSA_REORTH_PRO || o.reorth == SSA_REORTH_NONE,
       "unknown reorth mode %d", o.reorth);
+  REQ(o.reorth == SSA_REORTH_FULL || o.precision == SSA_PREC_F64,
+      "partial or no reorthogonalisation needs SSA_PREC_F64 (the FP32 products' error is above sqrt(eps))");
   REQ(o.grid_cap >= 0, "grid_cap must be >= 0 (got %d)", o.grid_cap);
   ssa_plan_s* p = new (std::nothrow) ssa_plan_s();
   if (!p) return SSA_ENOMEM;
@@ -828,6 +830,59 @@ static int ensure_workspace(ssa_plan_t p, int d) {
 
 static int refine_sigma(ssa_plan_t p, ssa_decomp_s* res, int k);
 
+// The Cullum-Willoughby selection (host only): sigma (c values, descending) are the singular
+// values of the projected matrix, sigma_hat (c_hat values) those of the matrix without its first
+// row, resid the residual estimates of sigma's Ritz pairs.  Values agree within 1e-10 sigma_1;
+// values at or below that are not candidates.  Walking sigma's groups of agreeing values in
+// descending order, a group of one value that agrees with some sigma_hat value is spurious; any
+// other group keeps its member with the smallest residual (lowest index on ties).  The first k kept
+// indices, padded with the largest unused indices when fewer pass, are written to keep in
+// ascending order; *converged = k passed and each kept residual is <= tol sigma_1.
+static int cw_select(const double* sig, int c, const double* sig2, int c2, const double* res, int k, double tol,
+                     int32_t* keep_out, int* converged) {
+  if (c < 1 || k < 1 || k > c || c2 < 0) return SSA_EINVAL;
+  const double same = 1e-10 * sig[0];  // two singular values agree within this
+  std::vector<int> keep;
+  for (int i = 0; i < c && (int)keep.size() < k && sig[i] > same;) {
+    int j = i;
+    while (j + 1 < c && sig[j + 1] >= sig[i] - same) ++j;
+    bool spurious = false;
+    if (j == i)
+      for (int t = 0; t < c2; ++t)
+        if (std::fabs(sig2[t] - sig[i]) <= same) spurious = true;
+    if (!spurious) {  // of several copies, the one whose Ritz pair has the smallest residual
+      int best = i;
+      for (int t = i + 1; t <= j; ++t)
+        if (res[t] < res[best]) best = t;
+      keep.push_back(best);
+    }
+    i = j + 1;
+  }
+  bool ok = (int)keep.size() == k;
+  for (int i : keep) ok = ok && res[i] <= tol * sig[0];
+  std::vector<char> used(c, 0);
+  for (int i : keep) used[i] = 1;
+  for (int i = 0; i < c && (int)keep.size() < k; ++i)
+    if (!used[i]) keep.push_back(i);
+  std::sort(keep.begin(), keep.end());
+  for (int m = 0; m < k; ++m) keep_out[m] = keep[m];
+  *converged = ok ? 1 : 0;
+  return SSA_OK;
+}
+
+extern "C" int ssa_cw_filter(const double* sigma, int c, const double* sigma_hat, int c_hat, const double* resid,
+                             int k, double tol, int32_t* keep, int* converged) {
+  REQ(sigma != nullptr && resid != nullptr && keep != nullptr && converged != nullptr &&
+          (sigma_hat != nullptr || c_hat == 0),
+      "NULL argument");
+  REQ(c >= 1 && k >= 1 && k <= c && c_hat >= 0, "need 1 <= k <= c and c_hat >= 0");
+  for (int i = 0; i < c; ++i) {
+    REQ(std::isfinite(sigma[i]) && std::isfinite(resid[i]), "non-finite sigma or residual at %d", i);
+    REQ(i == 0 || sigma[i] <= sigma[i - 1], "sigma must be in descending order");
+  }
+  return cw_select(sigma, c, sigma_hat, c_hat, resid, k, tol, keep, converged);
+}
+
 // Cullum-Willoughby filtering of a bidiagonalisation run without reorthogonalisation
 // (section 3.2.1): the projected matrix B (r x c) is the Golub-Kahan tridiagonal of the
 // Lanczos process started from u_1; a simple singular value of B that is also a singular
@@ -846,31 +901,10 @@ static int ghost_filter(Workspace& w, int r, int c, int k, double tol, int* conv
   CK(cudaMemcpyAsync(sig2.data(), w.sw2.sigma_d, c * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(res.data(), w.sw.resid, c * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  const double same = 1e-10 * sig[0];  // two singular values agree within this
-  std::vector<int> keep;
-  for (int i = 0; i < c && (int)keep.size() < k && sig[i] > same;) {
-    int j = i;
-    while (j + 1 < c && sig[j + 1] >= sig[i] - same) ++j;
-    bool spurious = false;
-    if (j == i)
-      for (int t = 0; t < c; ++t)
-        if (std::fabs(sig2[t] - sig[i]) <= same) spurious = true;
-    if (!spurious) {  // of several copies, the one whose Ritz pair has the smallest residual
-      int best = i;
-      for (int t = i + 1; t <= j; ++t)
-        if (res[t] < res[best]) best = t;
-      keep.push_back(best);
-    }
-    i = j + 1;
-  }
-  bool ok = (int)keep.size() == k;
-  for (int i : keep) ok = ok && res[i] <= tol * sig[0];
-  std::vector<char> used(c, 0);
-  for (int i : keep) used[i] = 1;
-  for (int i = 0; i < c && (int)keep.size() < k; ++i)
-    if (!used[i]) keep.push_back(i);
-  std::sort(keep.begin(), keep.end());
-  *converged = ok ? 1 : 0;
+  std::vector<int32_t> keep(k);
+  int ok = 0;
+  if (cw_select(sig.data(), c, sig2.data(), c, res.data(), k, tol, keep.data(), &ok) != SSA_OK) return SSA_EINVAL;
+  *converged = ok;
   // gather the kept columns into the first k places (host round trip of the small matrices)
   std::vector<df64> P((size_t)r * c), Q((size_t)c * c), sg(c);
   std::vector<double> sd(c);

@@ -341,3 +341,7 @@ def test_no_reorthogonalisation_reports_what_it_misses():
     assert np.all(np.isfinite(s)) and np.all(np.diff(s) <= 0)
     ref = load_golden("sigma_three_sines_N5113_L2556_k100.txt")["sigma"]
     assert np.max(np.abs(s[:10] - ref[:10]) / ref[:10]) <= SIG_F64
+    # the opt-in modes are refused with FP32 products (their error is above sqrt(eps))
+    for mode in (ssa.SSA_REORTH_NONE, ssa.SSA_REORTH_PRO):
+        with pytest.raises(ssa.SSAError):
+            gpu_decompose(f, L, k, precision=ssa.SSA_PREC_F32C, reorth=mode)
