@@ -329,6 +329,24 @@ struct ssa_plan_s {
   int fexp = 0;
   unsigned long long* fstat = nullptr;  // device: [0] max |f| (bits), [1] non-finite count
   Workspace ws;
+  // CUDA graphs of whole Lanczos cycles (the half-steps between two convergence tests), keyed by
+  // their shape; a shape is captured the second time it runs with this workspace, so that a plan
+  // used once pays no capture
+  struct CycleGraph {
+    int cur, r0, c0, d;
+    bool pro, none;
+    bool captured, failed;
+    cudaGraphExec_t exec;
+    int dr, dc;
+    int64_t dmv;
+    uint64_t launches;
+  };
+  std::vector<CycleGraph> cycles;
+  void drop_cycles() {
+    for (auto& e : cycles)
+      if (e.exec) cudaGraphExecDestroy(e.exec);
+    cycles.clear();
+  }
 };
 
 struct ssa_decomp_s {
@@ -381,6 +399,16 @@ static cudaEvent_t ev_get() {
   return e;
 }
 bool prof_enabled() { return g_pon; }
+static thread_local uint64_t t_launches = 0;
+uint64_t prof_thread_launches() { return t_launches; }
+void prof_add_launches(uint64_t n) {
+  g_launches += n;
+  t_launches += n;
+}
+void prof_sub_launches(uint64_t n) {
+  g_launches -= n;
+  t_launches -= n;
+}
 void prof_begin(cudaStream_t s) {
   if (!g_pon || g_psup) return;
   std::lock_guard<std::mutex> lk(g_pmu);
@@ -389,6 +417,7 @@ void prof_begin(cudaStream_t s) {
 }
 void prof_end(cudaStream_t s, int cls, double bytes, double flops, int launches) {
   g_launches += launches;
+  t_launches += launches;
   if (!g_pon || g_psup || !g_begin) return;
   std::lock_guard<std::mutex> lk(g_pmu);
   cudaEvent_t e = ev_get();
@@ -493,6 +522,7 @@ extern "C" const char* ssa_last_error(void) { return g_err; }
 
 extern "C" void ssa_plan_destroy(ssa_plan_t p) {
   if (!p) return;
+  p->drop_cycles();
   p->ws.release(p->stream);
   free_async(p->tw, p->stream);
   free_async(p->tA, p->stream);
@@ -766,6 +796,7 @@ static int ensure_workspace(ssa_plan_t p, int d) {
   Workspace& w = p->ws;
   if (w.dcap >= d) return SSA_OK;
   cudaStream_t st = p->stream;
+  p->drop_cycles();  // their kernels point into the old workspace
   w.release(st);
   const int cols = d + 2;
   w.ldu = (p->Lw + 3) / 4 * 4;
@@ -964,7 +995,10 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
   w.sw.max_sweeps = 60;
   w.sw.rot_tol = 1e-13f;
   const uint64_t seed = p->opts.seed;
-  uint64_t stream_id = 1;  // counter streams of the breakdown replacements (0: the starting vector)
+  // counter streams of the random vectors: 0 the starting vector, 1 its breakdown replacement, and
+  // 2 + 2 j (+1 on the v side) the replacement of the j-th vector of a side, so that a half-step's
+  // launches depend only on its position (a cycle replays from a CUDA graph unchanged)
+  auto sid = [](int j, bool vside) { return (uint64_t)2 + 2 * (uint64_t)j + (vside ? 1 : 0); };
   int64_t matvecs = 0;
   // one reorthogonalisation pass suffices when the products are FP32 (their
   // error, ~1e-7 sigma_1, is far above one pass's df64 orthogonality)
@@ -996,9 +1030,8 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
       w.rw.nrm_blocks = 0;  // the normalisation takes *rw.nrm
       w.rw.skip_flag = nullptr;
       df64* qcol = Qb + (int64_t)ncols * ldq;
-      CK((cudaError_t)launch_normalize_coop(w.y, dim, w.rw, qcol, bentry, w.est, Qb, ldq, ncols, seed, stream_id,
-                                            w.status, s));
-      ++stream_id;
+      CK((cudaError_t)launch_normalize_coop(w.y, dim, w.rw, qcol, bentry, w.est, Qb, ldq, ncols, seed,
+                                            sid(ncols, vside), w.status, s));
       CHECK_LAUNCH();
       if (vside) ++c;
       else ++r;
@@ -1016,9 +1049,8 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     }
     launch_cgs2(Qb, ldq, ncols, w.y, dim, w.rw, mode, s);
     df64* qcol = Qb + (int64_t)ncols * ldq;
-    CK((cudaError_t)launch_normalize_coop(w.y, dim, w.rw, qcol, bentry, w.est, Qb, ldq, ncols, seed, stream_id,
-                                          w.status, s));
-    ++stream_id;
+    CK((cudaError_t)launch_normalize_coop(w.y, dim, w.rw, qcol, bentry, w.est, Qb, ldq, ncols, seed,
+                                          sid(ncols, vside), w.status, s));
     CHECK_LAUNCH();
     if (vside) ++c;
     else ++r;
@@ -1031,24 +1063,91 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     if (pro || none) launch_pro_reset(w.pro, s);
     launch_random_fill(w.y, Lw, seed, 0, s);
     launch_cgs2(U, w.ldu, 0, w.y, Lw, w.rw, reorth, s);
-    CK((cudaError_t)launch_normalize_coop(w.y, Lw, w.rw, U, w.dummy, w.est, U, w.ldu, 0, seed, stream_id++,
+    CK((cudaError_t)launch_normalize_coop(w.y, Lw, w.rw, U, w.dummy, w.est, U, w.ldu, 0, seed, 1,
                                           w.status, s));
     CHECK_LAUNCH();
     r = 1;
     c = 0;
     return side(true);
   };
+  // one cycle of half-steps up to the Krylov dimension; every decision inside it is taken on the
+  // device, so its launches depend only on (cur, r, c, d, mode) and it replays from a CUDA graph
+  auto plain_cycle = [&]() -> int {
+    while (c < d + 1) {
+      int e = side(false);
+      if (e) return e;
+      e = side(true);
+      if (e) return e;
+    }
+    return SSA_OK;
+  };
+  auto run_cycle = [&]() -> int {
+    if (prof_enabled()) return plain_cycle();  // per-launch events and host reads: no graph
+    int idx = -1;
+    for (size_t i = 0; i < p->cycles.size(); ++i) {
+      const auto& e = p->cycles[i];
+      if (e.cur == cur && e.r0 == r && e.c0 == c && e.d == d && e.pro == pro && e.none == none) idx = (int)i;
+    }
+    if (idx < 0) {  // first time: run it and remember the shape
+      p->cycles.push_back({cur, r, c, d, pro, none, false, false, nullptr, 0, 0, 0, 0});
+      return plain_cycle();
+    }
+    if (p->cycles[idx].failed) return plain_cycle();
+    if (p->cycles[idx].captured) {
+      auto& e = p->cycles[idx];
+      CK(cudaGraphLaunch(e.exec, s));
+      prof_add_launches(e.launches);
+      r += e.dr;
+      c += e.dc;
+      matvecs += e.dmv;
+      return SSA_OK;
+    }
+    // second time: capture (nothing runs during the capture), instantiate, launch
+    const int r0 = r, c0 = c;
+    const int64_t mv0 = matvecs;
+    const uint64_t l0 = prof_thread_launches();
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    int rc2 = e == cudaSuccess ? plain_cycle() : SSA_ECUDA;
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(s, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc2 == SSA_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    const uint64_t nl = prof_thread_launches() - l0;
+    const int dr = r - r0, dc = c - c0;
+    const int64_t dmv = matvecs - mv0;
+    // the captured launches did not run: undo the host-side bookkeeping
+    r = r0;
+    c = c0;
+    matvecs = mv0;
+    prof_sub_launches(nl);
+    if (rc2 != SSA_OK || e != cudaSuccess || !exec) {  // not capturable here: run it as before
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      p->cycles[idx].failed = true;
+      return plain_cycle();
+    }
+    auto& ent = p->cycles[idx];
+    ent.exec = exec;
+    ent.captured = true;
+    ent.launches = nl;
+    ent.dr = dr;
+    ent.dc = dc;
+    ent.dmv = dmv;
+    CK(cudaGraphLaunch(exec, s));
+    prof_add_launches(nl);
+    r += ent.dr;
+    c += ent.dc;
+    matvecs += ent.dmv;
+    return SSA_OK;
+  };
   int restarts = 0, converged = 0;
   rc = start();
   if (rc) return rc;
   unsigned status = 0;
   for (;;) {
-    while (c < d + 1) {
-      rc = side(false);
-      if (rc) return rc;
-      rc = side(true);
-      if (rc) return rc;
-    }
+    rc = run_cycle();
+    if (rc) return rc;
     const int cp = c - 1;
     launch_small_svd(w.B, w.ldb, r, cp, w.sw, k, tol, w.est, w.status, s);
     CHECK_LAUNCH();

@@ -32,6 +32,11 @@ void prof_begin(cudaStream_t s);
 void prof_end(cudaStream_t s, int cls, double bytes, double flops, int launches = 1);
 void prof_flush();
 bool prof_enabled();
+// launches counted on the calling thread (for the launch count of a captured CUDA graph), and
+// launches replayed from such a graph
+uint64_t prof_thread_launches();
+void prof_add_launches(uint64_t n);
+void prof_sub_launches(uint64_t n);
 // while on (this thread), launches are counted but not timed (no host allocation)
 void prof_suppress(bool on);
 void host_set_error(const char* msg);

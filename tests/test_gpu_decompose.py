@@ -345,3 +345,36 @@ def test_no_reorthogonalisation_reports_what_it_misses():
     for mode in (ssa.SSA_REORTH_NONE, ssa.SSA_REORTH_PRO):
         with pytest.raises(ssa.SSAError):
             gpu_decompose(f, L, k, precision=ssa.SSA_PREC_F32C, reorth=mode)
+
+
+@pytest.mark.parametrize("N,L,k,kw", [(40000, 13333, 20, {}), (70000, 35000, 30, {"reorth_skip": 1e-12}),
+                                      (5000, 2500, 8, {"reorth": ssa.SSA_REORTH_PRO}), (1000, 500, 10, {})])
+def test_repeated_decompositions_replay_cycles_exactly(N, L, k, kw):
+    """A plan that decomposes again runs each Lanczos cycle from a CUDA graph (captured on the
+    second run of a cycle shape, replayed after): the first, second and third decompositions of
+    the same series give the same sigma, vectors and launch count, bit for bit."""
+    f = synth.many_sines(N, seed=N + k)
+    K = N - L + 1
+    plan = ssa.ssa_embed_plan(N, L, ssa.make_opts(**kw))
+    try:
+        outs = []
+        for _ in range(3):
+            l0 = ssa.ssa_kernel_launches()
+            d, rc = ssa.ssa_decompose(plan, f, k)
+            try:
+                sigma, U, V = np.empty(k), np.empty((k, L)), np.empty((k, K))
+                ssa.ssa_decomp_get(d, sigma, U, V, None)
+                info = ssa.ssa_decomp_info(d)
+            finally:
+                ssa.ssa_decomp_destroy(d)
+            outs.append((rc, sigma, U, V, info, ssa.ssa_kernel_launches() - l0))
+        for rc, sigma, U, V, info, nl in outs[1:]:
+            assert rc == outs[0][0] == ssa.SSA_OK
+            assert np.array_equal(sigma, outs[0][1])
+            assert np.array_equal(U, outs[0][2]) and np.array_equal(V, outs[0][3])
+            assert info == outs[0][4]
+            assert nl == outs[0][5]
+    finally:
+        ssa.ssa_plan_destroy(plan)
+    ref = ossa.decompose(f, L, k, method="jacobi" if N <= 1500 else "lanczos")
+    assert np.max(_rel(outs[2][1], ref["sigma"])) <= SIG_F64
