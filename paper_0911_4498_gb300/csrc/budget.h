@@ -18,6 +18,10 @@ int64_t batch_path_bytes(const std::vector<BatchItem>& items, int refine);
 // a series can run in the batched engine
 bool batch_eligible(int64_t N, int64_t L, int k, int precision);
 
+// raise (never lower) the freed device memory that the library's own stream-ordered pool keeps
+// for reuse on the current device (default 4 GiB); the request server keeps its whole budget
+void lib_pool_keep(uint64_t bytes);
+
 }  // namespace ssa
 
 // device array of all left vectors of a batch (series after series, each

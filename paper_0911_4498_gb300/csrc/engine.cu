@@ -97,6 +97,17 @@ static cudaMemPool_t lib_pool() {
   return pools[dev];
 }
 
+namespace ssa {
+void lib_pool_keep(uint64_t bytes) {
+  cudaMemPool_t pool = lib_pool();
+  if (!pool) return;
+  uint64_t cur = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && bytes > cur)
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &bytes);
+  cudaGetLastError();
+}
+}  // namespace ssa
+
 template <class T> static cudaError_t dev_alloc(T** ptr, size_t bytes, cudaStream_t s) {
   int64_t v = g_fail_after.load();
   while (v >= 0) {
@@ -330,11 +341,14 @@ struct ssa_plan_s {
   unsigned long long* fstat = nullptr;  // device: [0] max |f| (bits), [1] non-finite count
   Workspace ws;
   // CUDA graphs of whole Lanczos cycles (the half-steps between two convergence tests), keyed by
-  // their shape; a shape is captured the second time it runs with this workspace, so that a plan
-  // used once pays no capture
+  // their shape; a shape is captured when it runs again in a later decomposition with this
+  // workspace (restart cycles repeat shapes within one decomposition, and a graph captured there
+  // would be replayed once or twice at most), so that a plan used once pays no capture
+  int64_t lanczos_calls = 0;
   struct CycleGraph {
     int cur, r0, c0, d;
     bool pro, none;
+    int64_t first_call;
     bool captured, failed;
     cudaGraphExec_t exec;
     int dr, dc;
@@ -1081,6 +1095,7 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
     }
     return SSA_OK;
   };
+  const int64_t call = ++p->lanczos_calls;
   auto run_cycle = [&]() -> int {
     if (prof_enabled()) return plain_cycle();  // per-launch events and host reads: no graph
     int idx = -1;
@@ -1089,10 +1104,10 @@ static int lanczos(ssa_plan_t p, int k, ssa_decomp_s* res) {
       if (e.cur == cur && e.r0 == r && e.c0 == c && e.d == d && e.pro == pro && e.none == none) idx = (int)i;
     }
     if (idx < 0) {  // first time: run it and remember the shape
-      p->cycles.push_back({cur, r, c, d, pro, none, false, false, nullptr, 0, 0, 0, 0});
+      p->cycles.push_back({cur, r, c, d, pro, none, call, false, false, nullptr, 0, 0, 0, 0});
       return plain_cycle();
     }
-    if (p->cycles[idx].failed) return plain_cycle();
+    if (p->cycles[idx].failed || p->cycles[idx].first_call == call) return plain_cycle();
     if (p->cycles[idx].captured) {
       auto& e = p->cycles[idx];
       CK(cudaGraphLaunch(e.exec, s));

@@ -320,6 +320,7 @@ extern "C" int ssa_serve_create(const ssa_serve_opts_t* opts, ssa_server_t* out)
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   cudaGetLastError();
+  ssa::lib_pool_keep((uint64_t)o.mem_budget);  // the single-series path allocates from this one
   for (int i = 0; i < o.workers; ++i) S->threads.emplace_back(single_worker, S);
   for (int i = 0; i < o.batch_workers; ++i) S->threads.emplace_back(batch_worker, S);
   *out = S;
