@@ -66,7 +66,7 @@ static bool is_device_ptr(const void* p) {
 static std::atomic<int64_t> g_fail_after{-1};
 // The library's stream-ordered allocations come from its own memory pool on each device, which
 // keeps up to 4 GiB of freed memory for reuse.  The device's default pool hands freed memory
-// back to the driver at every synchronisation, so the per-call scratch of the reconstruction
+// back to the CUDA driver at every synchronisation, so the per-call scratch of the reconstruction
 // (about 1.3 GB at N = 2^20) and host-output staging were mapped again on every call.
 static cudaMemPool_t lib_pool() {
   static std::mutex mu;

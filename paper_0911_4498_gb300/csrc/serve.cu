@@ -313,7 +313,7 @@ extern "C" int ssa_serve_create(const ssa_serve_opts_t* opts, ssa_server_t* out)
   S->grid_cap = o.grid_cap;
   S->t0 = std::chrono::steady_clock::now();
   // keep freed stream-ordered memory in the pool so that per-request
-  // allocations are served without returning to the driver
+  // allocations are served without returning to the CUDA driver
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, S->dev) == cudaSuccess) {
     uint64_t thr = (uint64_t)o.mem_budget;
