@@ -661,6 +661,7 @@ def run_gpu_serving(args, w):
             "config": {"workload": args.workload, "arrival_rate": w["rate"], "N": "log-uniform [1e3, 1e6]",
                        "L": "N//2", "k": "U{2..64}", "mem_budget_GiB": 40, "precision": args.precision_batch,
                        "outputs": "sigma and residuals", "workers": args.serve_workers,
+                       "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8 (default)"),
                        "batch_workers": args.serve_batch_workers, "max_batch": args.serve_max_batch,
                        "grid_cap": args.serve_grid_cap,
                        "series_pool": P, "capacity_sample": len(ids),
@@ -1240,7 +1241,9 @@ def main():
     ap.add_argument("--serve-max-batch", type=int, default=128, help="serving: requests per batched launch at most")
     ap.add_argument("--seq-sample", type=int, default=0,
                     help="serving: pool entries timed one after another in FP64 (0 = all of them)")
-    ap.add_argument("--serve-workers", type=int, default=8, help="serving: single-series workers (streams)")
+    ap.add_argument("--serve-workers", type=int, default=16, help="serving: single-series workers (streams)")
+    ap.add_argument("--serve-connections", type=int, default=32,
+                    help="serving: CUDA_DEVICE_MAX_CONNECTIONS (hardware work queues) unless already set")
     ap.add_argument("--serve-grid-cap", type=int, default=0,
                     help="serving: CTAs per persistent kernel of a request (0 = the whole device)")
     ap.add_argument("--serve-batch-workers", type=int, default=1, help="serving: batched-launch workers")
@@ -1250,6 +1253,10 @@ def main():
         return 0
     if args.impl == "reference":
         return run_reference(args)
+    if WORKLOADS[args.workload].get("kind") == "serving":
+        # 16 single-series streams share 8 hardware work queues by default; read when the CUDA
+        # context is created, so set before the first CUDA call of this process
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", str(args.serve_connections))
     return run_gpu(args)
 
 

@@ -312,7 +312,11 @@ typedef struct ssa_serve_opts {
   int precision;        /* SSA_PREC_F64 or SSA_PREC_F32C for every request (default SSA_PREC_F32C) */
   double tol;           /* as ssa_opts_t.tol (0 = the precision's default) */
   int64_t mem_budget;   /* device bytes that admitted requests may hold together (default 40 GiB) */
-  int workers;          /* single-series requests running at once (default 8, at most 64) */
+  int workers;          /* single-series requests running at once (default 8, at most 64).  Every worker
+                           has its own stream, and CUDA maps streams onto 8 hardware work queues unless
+                           CUDA_DEVICE_MAX_CONNECTIONS is raised before the process creates its CUDA
+                           context: measured on the 2000 req/s mix, 16 workers with 32 connections
+                           served 80 requests/s, 8 workers 77, 16 workers with 8 connections 71 */
   int batch_workers;    /* batched launches running at once (default 1, at most 16; 0 = never batch) */
   int max_batch;        /* requests per batched launch (default 128) */
   int64_t batch_max_n;  /* only series with N <= this are batched (0 = the engine's limit, -1 = none) */
