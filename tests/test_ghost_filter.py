@@ -27,6 +27,20 @@ def _run(steps):
     return B, V, s, s_hat, res
 
 
+@pytest.mark.parametrize("steps", [60, 120])
+def test_oracle_recurrence_holds_without_orthogonality(steps):
+    """Algorithm 1's two relations hold to rounding however far the vectors have lost orthogonality:
+    A V = U B (u-side recurrence) and A^T U_s = V B_s^T (v-side, with B_s the first s rows of B);
+    unit-length Lanczos vectors."""
+    A = _matrix()
+    B, alpha_next, U, V = ghost.gkl_no_reorth(lambda x: A @ x, lambda x: A.T @ x, np.ones(A.shape[0]), steps)
+    nA = np.linalg.norm(A)
+    assert np.linalg.norm(A @ V - U @ B) <= 1e-14 * nA
+    assert np.linalg.norm(A.T @ U[:, :steps] - V @ B[:steps, :].T) <= 1e-14 * nA
+    assert np.allclose(np.linalg.norm(U, axis=0), 1.0) and np.allclose(np.linalg.norm(V, axis=0), 1.0)
+    assert np.max(np.abs(V.T @ V - np.eye(steps))) > 0.5   # while orthogonality is gone
+
+
 @pytest.mark.parametrize("steps", [60, 90, 120])
 def test_oracle_filter_recovers_known_singular_values(steps):
     B, V, s, s_hat, res = _run(steps)
